@@ -1,0 +1,373 @@
+#!/usr/bin/env python3
+"""Benchmark: stable sort of 2^28 uint32 keys with uint32 index payloads.
+
+One step = one full sort (count pass + device plan + every digit-group pass)
+of the whole array, keys and payloads, through the C ABI.  Prints ONE JSON
+line (rank 0).  Workload: 2^28 u32 keys (uniform over [0, 2^32) for the
+headline ``value``; Zipf s=1.1 and 90%-presorted reported beside it), u32
+payload = input index, synthetic and seeded.  Inputs (2 GiB) are larger than
+the 129 MB L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+``--impl reference`` times the plain CPU oracle (the paper's algorithm, single
+thread) on a bounded sample of the same workload and prints the same line
+with ``"impl": "reference"``.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "keys/s (2^28 u32) & HBM GB/s vs peak; batched vs per-call segmented keys/s"
+N_KEYS = 1 << 28
+ORACLE_SAMPLE = 1 << 24        # cpu_baseline: oracle on the first 2^24 pairs (~6-10 s)
+REFERENCE_STEP_SAMPLE = 1 << 22
+PASS_BYTES_PER_KEY = 16        # one digit-group pass moves key+value in and out: 4+4+4+4
+COUNT_BYTES_PER_KEY = 4        # the counting pass reads each key once
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "pass_kernel_u32_pairs_2p28.md")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--dists", default="uniform,zipf,presorted")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.3)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 8:
+                    continue
+                try:
+                    rows.append((float(parts[0]), float(parts[1]), parts[3:8]))
+                except ValueError:
+                    continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        smax = max(r[1] for r in rows)
+        loaded = [r for r in rows if r[0] > 0.5 * smax] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in loaded for i, v in enumerate(r[2][1:5])
+                          if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": smax,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def profile_traffic(kernel_source_hash: str):
+    """Per-launch DRAM bytes of the pass kernel from the committed ncu summary,
+    or None when absent or taken on a different kernel source."""
+    if not os.path.exists(PROFILE_SUMMARY):
+        return None
+    vals = {}
+    with open(PROFILE_SUMMARY) as f:
+        for line in f:
+            if ":" in line and line.startswith("- "):
+                k, _, v = line[2:].partition(":")
+                vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_sha256") != kernel_source_hash:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in ("rs_device.cuh", "rs_kernels.cuh"):
+        with open(os.path.join(ROOT, "paper_2107_01391_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def cpu_baseline(sample_n: int):
+    """The oracle, as it stands, on the first sample_n pairs of the workload."""
+    from oracle import oracle
+    from paper_2107_01391_gb300 import workloads as W
+    keys, vals = W.u32_pairs(sample_n, "uniform")
+    t0 = time.perf_counter()
+    oracle.sort_pairs(keys, vals)
+    dt = time.perf_counter() - t0
+    return {"value": sample_n / dt, "unit": "keys/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {sample_n} keys (2^{int(np.log2(sample_n))}) of the uniform "
+                      f"u32-pairs workload, one oracle call, {dt:.2f} s single-threaded"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from oracle import oracle
+    from paper_2107_01391_gb300 import workloads as W
+    oracle.build()
+    keys, vals = W.u32_pairs(REFERENCE_STEP_SAMPLE, "uniform")
+    for _ in range(args.warmup):
+        oracle.sort_pairs(keys, vals)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.sort_pairs(keys, vals)
+    dt = (time.perf_counter() - t0) / max(args.steps, 1)
+    value = REFERENCE_STEP_SAMPLE / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "keys/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "2^28 u32 keys + u32 index payload, uniform over [0,2^32)",
+                   "n": N_KEYS, "step_sample": REFERENCE_STEP_SAMPLE},
+        "cpu_baseline": {"value": value, "unit": "keys/s", "cores": 1, "kind": "oracle",
+                         "sample": f"each step sorts the first {REFERENCE_STEP_SAMPLE} keys "
+                                   "of the workload with the single-threaded oracle"},
+        "e2e": {"value": value, "unit": "keys/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2107_01391_gb300 import build, binding, workloads as W
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    build.build()
+    ctx = binding.Context(local)
+    stream = torch.cuda.current_stream()
+    n = N_KEYS
+    hbm_peak, peak_kind = peaks()
+    dists = [d for d in args.dists.split(",") if d]
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    results = {}
+    for dname in dists:
+        keys_h, vals_h = W.u32_pairs(n, dname, seed_extra=rank)
+        dk = torch.from_numpy(keys_h.view(np.int32)).cuda()
+        dv = torch.from_numpy(vals_h.view(np.int32)).cuda()
+        ko, vo = torch.empty_like(dk), torch.empty_like(dv)
+        temp = torch.empty(binding.workspace_bytes("rs_sort_pairs_u32", n), dtype=torch.uint8,
+                           device="cuda")
+        for _ in range(args.warmup):
+            binding.rs_sort_pairs(dk, dv, ko, vo, ctx=ctx, temp=temp)
+        ctx.check()
+        headline = dname == dists[0]
+        ctx.reset_timing()
+        ctx.set_timing(True)
+        launches0 = ctx.launch_count()
+        barrier()
+        sampler = ClockSampler(local) if headline else None
+        if sampler:
+            sampler.__enter__()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            binding.rs_sort_pairs(dk, dv, ko, vo, ctx=ctx, temp=temp)
+        e1.record(stream)
+        barrier()
+        if sampler:
+            sampler.__exit__(None, None, None)
+        ctx.set_timing(False)
+        ctx.check()
+        ms = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+        pass_ms, pass_launches = ctx.kernel_time("pass")
+        count_ms, count_launches = ctx.kernel_time("hist")
+        plan = ctx.last_plan()
+        results[dname] = {
+            "ms_per_step": ms, "keys_per_s": world * n / (ms * 1e-3),
+            "pass_ms_avg": pass_ms / max(pass_launches, 1),
+            "count_ms_avg": count_ms / max(count_launches, 1),
+            "passes_run": plan["passes_run"],
+            "launches_per_step": (ctx.launch_count() - launches0) / args.steps,
+            "clocks": sampler.summary() if sampler else None,
+        }
+        # spot check of the sorted output (full parity lives in the tests)
+        k_chk = ko[: 1 << 20].to(torch.int64) & 0xFFFFFFFF
+        assert bool((k_chk[1:] >= k_chk[:-1]).all()), "output not sorted"
+        del dk, dv, ko, vo, temp
+        torch.cuda.empty_cache()
+
+    # end to end through the C ABI: pinned host keys+values in, sorted out
+    e2e = None
+    if not args.no_e2e:
+        keys_h, vals_h = W.u32_pairs(n, dists[0], seed_extra=rank)
+        hk = torch.from_numpy(keys_h.view(np.int32)).pin_memory()
+        hv = torch.from_numpy(vals_h.view(np.int32)).pin_memory()
+        ok_h, ov_h = torch.empty_like(hk).pin_memory(), torch.empty_like(hv).pin_memory()
+        dk, dv = torch.empty(n, dtype=torch.int32, device="cuda"), torch.empty(
+            n, dtype=torch.int32, device="cuda")
+        ko, vo = torch.empty_like(dk), torch.empty_like(dv)
+        temp = torch.empty(binding.workspace_bytes("rs_sort_pairs_u32", n), dtype=torch.uint8,
+                           device="cuda")
+
+        def e2e_step():
+            dk.copy_(hk, non_blocking=True)
+            dv.copy_(hv, non_blocking=True)
+            binding.rs_sort_pairs(dk, dv, ko, vo, ctx=ctx, temp=temp)
+            ok_h.copy_(ko, non_blocking=True)
+            ov_h.copy_(vo, non_blocking=True)
+
+        for _ in range(max(1, min(args.warmup, 3))):
+            e2e_step()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        steps = max(1, min(args.steps, 10))
+        e0.record(stream)
+        for _ in range(steps):
+            e2e_step()
+        e1.record(stream)
+        barrier()
+        ctx.check()
+        ms_e2e = max_over_ranks(e0.elapsed_time(e1) / steps)
+        e2e = {"value": world * n / (ms_e2e * 1e-3), "unit": "keys/s",
+               "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n,
+               "ms_per_step": ms_e2e, "steps": steps}
+        del dk, dv, ko, vo, temp
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+    head = results[dists[0]]
+    pass_ms = head["pass_ms_avg"]
+    achieved = PASS_BYTES_PER_KEY * n / (pass_ms * 1e-3) / 1e9
+    traffic = profile_traffic(kernel_source_hash())
+    line = {
+        "metric": METRIC,
+        "value": head["keys_per_s"],
+        "unit": "keys/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": head["ms_per_step"],
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u32",
+        "data": "synthetic",
+        "config": {
+            "workload": "2^28 u32 keys + u32 index payload (stable pairs sort), "
+                        f"{dists[0]} over [0,2^32)",
+            "n": n, "key": "u32", "value": "u32 index", "dist": dists[0],
+            "parallelism": f"replicas x{world}",
+            "l2": "inputs (2 GiB of keys+values) larger than the 129 MB L2; no flush",
+            "digit_bits": 8, "passes": head["passes_run"],
+            "alg_bytes_per_key": COUNT_BYTES_PER_KEY + PASS_BYTES_PER_KEY * head["passes_run"],
+        },
+        "hbm_gbs_alg": (COUNT_BYTES_PER_KEY + PASS_BYTES_PER_KEY * head["passes_run"]) * n
+                       / (head["ms_per_step"] * 1e-3) / 1e9,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": traffic,
+                     "kernel": "pass_kernel<CodecU32,u32,16>",
+                     "alg_bytes_per_launch": PASS_BYTES_PER_KEY * n,
+                     "launch_ms_avg": pass_ms, "peak_kind": f"{peak_kind} hbm_gbs"},
+        "clocks": head["clocks"],
+        "gpu_launches": int(round(head["launches_per_step"] * args.steps)),
+        "dists": {d: {"keys_per_s": r["keys_per_s"], "ms_per_step": r["ms_per_step"],
+                      "pass_ms_avg": r["pass_ms_avg"], "count_ms_avg": r["count_ms_avg"],
+                      "passes_run": r["passes_run"]} for d, r in results.items()},
+        "e2e": e2e,
+        "cpu_baseline": cpu_baseline(ORACLE_SAMPLE) if world == 1 else None,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,166 @@
+/*
+ * rs.h -- C ABI of the GB300 Recombinant Sort library (librsort.so).
+ *
+ * Recombinant Sort (Kumar et al., arXiv 2107.01391) maps each key to the
+ * cell of an N-dimensional Cartesian count space whose axes are the key's
+ * digits (Eq. 1, Eq. 2), counts the keys per cell (the hashing cycle, §3.1),
+ * walks the space in raster order to give each occupied cell its output
+ * position (the extraction cycle, §3.2, with the cursor overwrite_pos_at),
+ * and writes the keys out in that order, rebuilding keys from cell
+ * coordinates where the input is not needed (Eq. 16).  When the space does
+ * not fit on chip, the leading dimensions act as buckets (§2.2).
+ *
+ * Every sort here is STABLE: equal keys (and their payloads) keep their input
+ * order.  Order is ascending.
+ *
+ * Conventions shared by every call:
+ *   - All key/value/offset/output pointers are DEVICE pointers owned by the
+ *     caller.  The library never allocates per call: each sort takes a
+ *     caller-provided device workspace `temp`.  Call once with temp == NULL
+ *     to receive the required size in *temp_bytes (nothing is launched), then
+ *     again with a buffer of at least that many bytes (256-byte aligned).
+ *   - `keys_out` may equal `keys_in` (in-place, as the paper overwrites arr);
+ *     any other overlap is undefined.  The same holds for values.
+ *   - Work is enqueued asynchronously on `stream` (NULL = the legacy default
+ *     stream); the call returns before the sort finishes.
+ *   - Host-detectable errors return immediately with nothing launched:
+ *     RS_ERR_INVALID (NULL pointer with n > 0, misaligned pointer, n above
+ *     RS_MAX_N, bad digit counts), RS_ERR_TEMP_TOO_SMALL, RS_ERR_UNSUPPORTED.
+ *     A failed CUDA launch returns RS_ERR_CUDA.
+ *   - Device-detected errors (a key outside its declared digit space ->
+ *     RS_ERR_RANGE; a look-back wait that exceeded its bound ->
+ *     RS_ERR_TIMEOUT) are recorded in the context's status word and
+ *     returned by rs_ctx_status().  The output of such a call is unspecified.
+ *   - Pointers must be aligned to their element size.
+ */
+#ifndef RS_H
+#define RS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same object as cudaStream_t / CUstream. */
+typedef struct CUstream_st* rs_stream_t;
+
+typedef enum rs_status {
+    RS_OK = 0,
+    RS_ERR_INVALID = 1,
+    RS_ERR_RANGE = 2,
+    RS_ERR_TEMP_TOO_SMALL = 3,
+    RS_ERR_CUDA = 4,
+    RS_ERR_TIMEOUT = 5,
+    RS_ERR_UNSUPPORTED = 6
+} rs_status;
+
+/* Largest n any call accepts (per-tile look-back counts are 30-bit). */
+#define RS_MAX_N ((size_t)((1u << 30) - 1u))
+
+typedef enum rs_key_type {
+    RS_KEY_U32 = 0,     /* uint32_t */
+    RS_KEY_U64 = 1,     /* uint64_t */
+    RS_KEY_I64_DEC = 2  /* int64_t fixed-point decimal, see rs_key_params */
+} rs_key_type;
+
+/* Digit layout of a fixed-point decimal key (RS_KEY_I64_DEC): the value
+ * x.y is stored as the integer x.y * 10^frac_digits, and every key must
+ * satisfy |key| < 10^(int_digits + frac_digits), 1 <= int_digits +
+ * frac_digits <= 18.  frac_digits is the paper's λ, the digit count after the
+ * decimal point (§3.1.1, "digit_count_after_decimal"). */
+typedef struct rs_key_params {
+    int32_t int_digits;
+    int32_t frac_digits;
+} rs_key_params;
+
+typedef struct rs_ctx rs_ctx;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context bound to CUDA device `device`.  Allocates the context's
+ * 256-byte device status word once (the only allocation the library makes).
+ * RS_ERR_INVALID if ctx is NULL or the device does not exist. */
+rs_status rs_ctx_create(rs_ctx** ctx, int device);
+
+/* Free the context; waits for nothing (the caller must not destroy a context
+ * whose sorts are still running). */
+rs_status rs_ctx_destroy(rs_ctx* ctx);
+
+/* Device-detected error of the calls made since the last check, then clear
+ * it.  synchronize != 0: wait for the whole device first and read the device
+ * status word (RS_OK, RS_ERR_RANGE or RS_ERR_TIMEOUT; a CUDA failure while
+ * waiting gives RS_ERR_CUDA).  synchronize == 0: report only errors already
+ * known on the host, without touching the device. */
+rs_status rs_ctx_status(rs_ctx* ctx, int synchronize);
+
+/* ------------------------------------------------------------------ sorts */
+
+/* Sort n uint32 keys (keys only).  The paper's problem statement (the
+ * hashing and extraction cycles, §3.1-§3.2) with λ = 0.  When every key is
+ * below RS_FILL_CELLS the whole key space is one count array and the output
+ * is rebuilt from the counted cells (Eq. 16) without re-reading the keys;
+ * otherwise the key's 8-bit digit groups are the dimensions, sorted as
+ * buckets from the least significant group on. */
+#define RS_FILL_CELLS 4096u
+rs_status rs_sort_u32(rs_ctx* ctx, const uint32_t* keys_in, uint32_t* keys_out, size_t n,
+                      void* temp, size_t* temp_bytes, rs_stream_t stream);
+
+/* Sort n uint64 keys (keys only); same contract as rs_sort_u32. */
+rs_status rs_sort_u64(rs_ctx* ctx, const uint64_t* keys_in, uint64_t* keys_out, size_t n,
+                      void* temp, size_t* temp_bytes, rs_stream_t stream);
+
+/* Sort n fixed-point decimals (int64 scaled by 10^frac_digits, see
+ * rs_key_params): the paper's keys with λ = frac_digits digits after the
+ * decimal point, integers and decimals mixed (§3.1.2).  Negative keys sort
+ * below positive ones.  A key with |key| >= 10^(int_digits+frac_digits)
+ * raises RS_ERR_RANGE (device-detected). */
+rs_status rs_sort_fixed_decimal(rs_ctx* ctx, const int64_t* keys_in, int64_t* keys_out,
+                                size_t n, int int_digits, int frac_digits, void* temp,
+                                size_t* temp_bytes, rs_stream_t stream);
+
+/* Stable key/value sort: the value at input i travels with key i.
+ * kt selects the key type (params required for RS_KEY_I64_DEC, ignored
+ * otherwise); val_bytes is 4 or 8.  vals_in/vals_out are device arrays of n
+ * values. */
+rs_status rs_sort_pairs(rs_ctx* ctx, rs_key_type kt, const void* keys_in, void* keys_out,
+                        const void* vals_in, void* vals_out, size_t val_bytes, size_t n,
+                        const rs_key_params* params, void* temp, size_t* temp_bytes,
+                        rs_stream_t stream);
+
+/* ------------------------------------------------------------ diagnostics */
+
+/* What the device-side plan of the most recent sort on this context chose
+ * (synchronises the device).  mode: 0 = digit passes, 1 = one count array
+ * rebuilt from cells (Eq. 16).  passes_run: passes that moved data;
+ * passes_total: passes the key width allows. */
+typedef struct rs_plan_info {
+    uint32_t mode;
+    uint32_t passes_run;
+    uint32_t passes_total;
+    uint32_t tiles;
+} rs_plan_info;
+rs_status rs_ctx_last_plan(rs_ctx* ctx, rs_plan_info* info);
+
+/* Per-kernel timing with CUDA events recorded on the launching stream around
+ * every launch (off by default).  Kernel classes: "hist", "pass", "fill".
+ * rs_ctx_kernel_time() synchronises, sums the elapsed time of every launch
+ * of that class since timing was enabled or last reset, and returns it with
+ * the launch count.  At most 65536 launches per class are kept. */
+rs_status rs_ctx_set_timing(rs_ctx* ctx, int enable);
+rs_status rs_ctx_kernel_time(rs_ctx* ctx, const char* kernel_class, double* total_ms,
+                             uint64_t* launches);
+rs_status rs_ctx_reset_timing(rs_ctx* ctx);
+
+/* Kernels this context launched since creation (all classes). */
+uint64_t rs_ctx_launch_count(const rs_ctx* ctx);
+
+/* Library version string. */
+const char* rs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RS_H */

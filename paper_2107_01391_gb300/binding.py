@@ -1,0 +1,304 @@
+"""Thin Python binding of the C ABI in ``include/rs.h`` (``librsort.so``).
+
+Argument marshalling only: torch supplies device memory (outputs and the
+workspace) and the current CUDA stream; every step of the sort runs in the
+library's CUDA kernels.  There is no CPU fallback: without the built library
+or a CUDA device every call raises.
+
+The function names mirror the C entry points (``rs_sort_u32`` ...).  Each
+takes CUDA tensors, allocates the outputs and the workspace unless given,
+enqueues the sort on the current stream and returns without waiting.
+Device-side errors surface through ``Context.status(synchronize=True)``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "librsort.so")
+
+RS_OK, RS_ERR_INVALID, RS_ERR_RANGE, RS_ERR_TEMP_TOO_SMALL = 0, 1, 2, 3
+RS_ERR_CUDA, RS_ERR_TIMEOUT, RS_ERR_UNSUPPORTED = 4, 5, 6
+STATUS_NAMES = {0: "RS_OK", 1: "RS_ERR_INVALID", 2: "RS_ERR_RANGE", 3: "RS_ERR_TEMP_TOO_SMALL",
+                4: "RS_ERR_CUDA", 5: "RS_ERR_TIMEOUT", 6: "RS_ERR_UNSUPPORTED"}
+RS_KEY_U32, RS_KEY_U64, RS_KEY_I64_DEC = 0, 1, 2
+RS_MAX_N = (1 << 30) - 1
+RS_FILL_CELLS = 4096
+
+# Every function the header declares (the CPU test checks the export table).
+EXPORTS = ("rs_ctx_create", "rs_ctx_destroy", "rs_ctx_status", "rs_sort_u32", "rs_sort_u64",
+           "rs_sort_fixed_decimal", "rs_sort_pairs", "rs_ctx_last_plan", "rs_ctx_set_timing",
+           "rs_ctx_kernel_time", "rs_ctx_reset_timing", "rs_ctx_launch_count", "rs_version")
+
+
+class RsError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what} failed: {STATUS_NAMES.get(code, code)}")
+        self.code = code
+
+
+class KeyParams(ctypes.Structure):
+    _fields_ = [("int_digits", ctypes.c_int32), ("frac_digits", ctypes.c_int32)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_uint32), ("passes_run", ctypes.c_uint32),
+                ("passes_total", ctypes.c_uint32), ("tiles", ctypes.c_uint32)]
+
+
+_lib = None
+_lib_lock = threading.Lock()
+
+
+def lib() -> ctypes.CDLL:
+    """Load librsort.so (built by ``paper_2107_01391_gb300.build``); raise if absent."""
+    global _lib
+    with _lib_lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run paper_2107_01391_gb300/build.py "
+                               "(nvcc, sm_103a); there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        p, sz, st = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int
+        psz = ctypes.POINTER(ctypes.c_size_t)
+        L.rs_ctx_create.argtypes = [ctypes.POINTER(p), ctypes.c_int]
+        L.rs_ctx_destroy.argtypes = [p]
+        L.rs_ctx_status.argtypes = [p, ctypes.c_int]
+        L.rs_ctx_last_plan.argtypes = [p, ctypes.POINTER(PlanInfo)]
+        L.rs_ctx_set_timing.argtypes = [p, ctypes.c_int]
+        L.rs_ctx_reset_timing.argtypes = [p]
+        L.rs_ctx_kernel_time.argtypes = [p, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_uint64)]
+        L.rs_ctx_launch_count.argtypes = [p]
+        L.rs_ctx_launch_count.restype = ctypes.c_uint64
+        L.rs_version.restype = ctypes.c_char_p
+        L.rs_sort_u32.argtypes = [p, p, p, sz, p, psz, p]
+        L.rs_sort_u64.argtypes = [p, p, p, sz, p, psz, p]
+        L.rs_sort_fixed_decimal.argtypes = [p, p, p, sz, ctypes.c_int, ctypes.c_int, p, psz, p]
+        L.rs_sort_pairs.argtypes = [p, ctypes.c_int, p, p, p, p, sz, sz,
+                                    ctypes.POINTER(KeyParams), p, psz, p]
+        for name in ("rs_ctx_create", "rs_ctx_destroy", "rs_ctx_status", "rs_ctx_last_plan",
+                     "rs_ctx_set_timing", "rs_ctx_reset_timing", "rs_ctx_kernel_time",
+                     "rs_sort_u32", "rs_sort_u64", "rs_sort_fixed_decimal", "rs_sort_pairs"):
+            getattr(L, name).restype = st
+        _lib = L
+        return L
+
+
+def _check(code: int, what: str):
+    if code != RS_OK:
+        raise RsError(code, what)
+
+
+class Context:
+    """Owns an ``rs_ctx`` (the device status word and the timing state)."""
+
+    def __init__(self, device: int | None = None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("rsort needs a CUDA device; there is no CPU fallback")
+        self.device = torch.cuda.current_device() if device is None else int(device)
+        self._h = ctypes.c_void_p()
+        _check(lib().rs_ctx_create(ctypes.byref(self._h), self.device), "rs_ctx_create")
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            lib().rs_ctx_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def status(self, synchronize: bool = True) -> int:
+        return lib().rs_ctx_status(self._h, int(synchronize))
+
+    def check(self):
+        """Wait for the device and raise on a device-detected error."""
+        _check(self.status(True), "device-side sort")
+
+    def last_plan(self) -> dict:
+        info = PlanInfo()
+        _check(lib().rs_ctx_last_plan(self._h, ctypes.byref(info)), "rs_ctx_last_plan")
+        return {"mode": "fill" if info.mode == 1 else "passes", "passes_run": info.passes_run,
+                "passes_total": info.passes_total, "tiles": info.tiles}
+
+    def set_timing(self, enable: bool):
+        _check(lib().rs_ctx_set_timing(self._h, int(enable)), "rs_ctx_set_timing")
+
+    def reset_timing(self):
+        _check(lib().rs_ctx_reset_timing(self._h), "rs_ctx_reset_timing")
+
+    def kernel_time(self, kernel_class: str):
+        """(total milliseconds, launches) of one kernel class: hist, pass or fill."""
+        ms, n = ctypes.c_double(), ctypes.c_uint64()
+        _check(lib().rs_ctx_kernel_time(self._h, kernel_class.encode(), ctypes.byref(ms),
+                                        ctypes.byref(n)), "rs_ctx_kernel_time")
+        return ms.value, n.value
+
+    def launch_count(self) -> int:
+        return int(lib().rs_ctx_launch_count(self._h))
+
+
+_default_ctx: dict[int, Context] = {}
+
+
+def default_context(device: int | None = None) -> Context:
+    dev = torch.cuda.current_device() if device is None else int(device)
+    if dev not in _default_ctx:
+        _default_ctx[dev] = Context(dev)
+    return _default_ctx[dev]
+
+
+def _cuda(t: torch.Tensor, name: str, nbytes: int, dtypes) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype not in dtypes:
+        raise TypeError(f"{name}: dtype {t.dtype} not in {dtypes}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+def _stream(t: torch.Tensor, stream):
+    s = torch.cuda.current_stream(t.device) if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None and t.numel() else ctypes.c_void_p(0)
+
+
+def _workspace(query, device, temp):
+    need = ctypes.c_size_t(0)
+    _check(query(None, ctypes.byref(need)), "workspace query")
+    if temp is None or temp.numel() < need.value:
+        temp = torch.empty(max(need.value, 1), dtype=torch.uint8, device=device)
+    return temp, ctypes.c_size_t(temp.numel())
+
+
+U32_DTYPES = (torch.uint32, torch.int32)
+U64_DTYPES = (torch.uint64, torch.int64)
+
+
+def rs_sort_u32(keys: torch.Tensor, out: torch.Tensor | None = None, *, ctx: Context | None = None,
+                stream=None, temp: torch.Tensor | None = None) -> torch.Tensor:
+    """Stable ascending sort of uint32 keys (int32 tensors are read as their uint32 bits)."""
+    _cuda(keys, "keys", 4, U32_DTYPES)
+    out = torch.empty_like(keys) if out is None else _cuda(out, "out", 4, U32_DTYPES)
+    ctx = ctx or default_context(keys.device.index)
+    n, s, L = keys.numel(), _stream(keys, stream), lib()
+    temp, tb = _workspace(lambda t, b: L.rs_sort_u32(ctx.handle, _ptr(keys), _ptr(out), n, t, b, s),
+                          keys.device, temp)
+    _check(L.rs_sort_u32(ctx.handle, _ptr(keys), _ptr(out), n, _ptr(temp), ctypes.byref(tb), s),
+           "rs_sort_u32")
+    return out
+
+
+def rs_sort_u64(keys: torch.Tensor, out: torch.Tensor | None = None, *, ctx: Context | None = None,
+                stream=None, temp: torch.Tensor | None = None) -> torch.Tensor:
+    """Stable ascending sort of uint64 keys (int64 tensors are read as their uint64 bits)."""
+    _cuda(keys, "keys", 8, U64_DTYPES)
+    out = torch.empty_like(keys) if out is None else _cuda(out, "out", 8, U64_DTYPES)
+    ctx = ctx or default_context(keys.device.index)
+    n, s, L = keys.numel(), _stream(keys, stream), lib()
+    temp, tb = _workspace(lambda t, b: L.rs_sort_u64(ctx.handle, _ptr(keys), _ptr(out), n, t, b, s),
+                          keys.device, temp)
+    _check(L.rs_sort_u64(ctx.handle, _ptr(keys), _ptr(out), n, _ptr(temp), ctypes.byref(tb), s),
+           "rs_sort_u64")
+    return out
+
+
+def rs_sort_fixed_decimal(keys: torch.Tensor, int_digits: int, frac_digits: int,
+                          out: torch.Tensor | None = None, *, ctx: Context | None = None,
+                          stream=None, temp: torch.Tensor | None = None) -> torch.Tensor:
+    """Stable ascending sort of int64 fixed-point decimals scaled by 10^frac_digits."""
+    _cuda(keys, "keys", 8, (torch.int64,))
+    out = torch.empty_like(keys) if out is None else _cuda(out, "out", 8, (torch.int64,))
+    ctx = ctx or default_context(keys.device.index)
+    n, s, L = keys.numel(), _stream(keys, stream), lib()
+    temp, tb = _workspace(
+        lambda t, b: L.rs_sort_fixed_decimal(ctx.handle, _ptr(keys), _ptr(out), n, int_digits,
+                                             frac_digits, t, b, s), keys.device, temp)
+    _check(L.rs_sort_fixed_decimal(ctx.handle, _ptr(keys), _ptr(out), n, int_digits, frac_digits,
+                                   _ptr(temp), ctypes.byref(tb), s), "rs_sort_fixed_decimal")
+    return out
+
+
+def _key_type(keys: torch.Tensor, decimal: tuple[int, int] | None) -> int:
+    if decimal is not None:
+        _cuda(keys, "keys", 8, (torch.int64,))
+        return RS_KEY_I64_DEC
+    if keys.dtype in U32_DTYPES:
+        return RS_KEY_U32
+    if keys.dtype in U64_DTYPES:
+        return RS_KEY_U64
+    raise TypeError(f"unsupported key dtype {keys.dtype}")
+
+
+def rs_sort_pairs(keys: torch.Tensor, values: torch.Tensor, keys_out: torch.Tensor | None = None,
+                  values_out: torch.Tensor | None = None, *, decimal: tuple[int, int] | None = None,
+                  ctx: Context | None = None, stream=None, temp: torch.Tensor | None = None):
+    """Stable key/value sort; returns (sorted keys, values in the same order).
+
+    ``decimal=(int_digits, frac_digits)`` sorts int64 keys as fixed-point
+    decimals; otherwise 4-byte keys are uint32 and 8-byte keys uint64.
+    Values may be any 4- or 8-byte dtype (moved as raw bits).
+    """
+    kt = _key_type(keys, decimal)
+    _cuda(keys, "keys", keys.element_size(), (keys.dtype,))
+    if values.numel() != keys.numel():
+        raise ValueError("keys and values must have the same length")
+    vb = values.element_size()
+    if vb not in (4, 8):
+        raise TypeError("values must be 4 or 8 bytes per element")
+    _cuda(values, "values", vb, (values.dtype,))
+    keys_out = torch.empty_like(keys) if keys_out is None else keys_out
+    values_out = torch.empty_like(values) if values_out is None else values_out
+    ctx = ctx or default_context(keys.device.index)
+    prm = KeyParams(*(decimal or (0, 0)))
+    pp = ctypes.byref(prm)
+    n, s, L = keys.numel(), _stream(keys, stream), lib()
+
+    def call(t, b):
+        return L.rs_sort_pairs(ctx.handle, kt, _ptr(keys), _ptr(keys_out), _ptr(values),
+                               _ptr(values_out), vb, n, pp, t, b, s)
+
+    temp, tb = _workspace(call, keys.device, temp)
+    _check(call(_ptr(temp), ctypes.byref(tb)), "rs_sort_pairs")
+    return keys_out, values_out
+
+
+def workspace_bytes(fn_name: str, n: int, **kw) -> int:
+    """Workspace size a call of ``fn_name`` needs for n keys (no launch)."""
+    L = lib()
+    need = ctypes.c_size_t(0)
+    # A size query launches nothing and never dereferences the context or the
+    # key pointers; placeholders only have to pass the argument checks.
+    h = ctypes.c_void_p(1)
+    z = ctypes.c_void_p(256)
+    if fn_name == "rs_sort_u32":
+        code = L.rs_sort_u32(h, z, z, n, None, ctypes.byref(need), None)
+    elif fn_name == "rs_sort_u64":
+        code = L.rs_sort_u64(h, z, z, n, None, ctypes.byref(need), None)
+    elif fn_name == "rs_sort_pairs_u32":
+        code = L.rs_sort_pairs(h, RS_KEY_U32, z, z, z, z, kw.get("val_bytes", 4), n, None, None,
+                               ctypes.byref(need), None)
+    else:
+        raise ValueError(fn_name)
+    _check(code, f"{fn_name} workspace query")
+    return need.value
+
+
+def version() -> str:
+    return lib().rs_version().decode()

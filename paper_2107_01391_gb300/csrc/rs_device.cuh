@@ -1,0 +1,179 @@
+// rs_device.cuh -- device-side building blocks shared by the sort kernels.
+//
+// Vocabulary (Kumar et al., "Recombinant Sort", arXiv 2107.01391):
+//   key   -> its digit vector (Eq. 1) -> the row-major index of its cell in
+//            the count space S (Eq. 2).  For base-10 digits that index is the
+//            key itself (scaled by 10^λ for decimals), so a "cell" here is an
+//            unsigned integer whose raster order is the key order.
+//   digit group -> 8 bits of the cell index: one on-chip dimension group of
+//            256 cells.  Groups are counted (hashing cycle, §3.1), prefix-summed
+//            in raster order (extraction cycle, §3.2) and scattered stably,
+//            least significant group first; the more significant groups act
+//            as the paper's buckets (§2.2) for the groups below them.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rs {
+
+constexpr int RADIX_BITS = 8;
+constexpr int RADIX = 1 << RADIX_BITS;  // cells per digit group
+constexpr int MAX_PASSES = 8;           // 64-bit cells / 8-bit groups
+constexpr uint32_t FILL_CELLS = 4096;   // largest count array rebuilt from cells (Eq. 16)
+constexpr int BLOCK = 256;              // threads per CTA of every sort kernel
+constexpr int WARPS = BLOCK / 32;
+
+// Device status word bits (rs_ctx_status maps them to rs_status codes).
+constexpr uint32_t STATUS_RANGE = 1u;
+constexpr uint32_t STATUS_TIMEOUT = 2u;
+
+// Look-back words: 2 flag bits over a 30-bit count.
+constexpr uint32_t LB_AGGREGATE = 1u << 30;  // this tile's own count only
+constexpr uint32_t LB_INCLUSIVE = 2u << 30;  // count of this tile and all before it
+constexpr uint32_t LB_VALUE = (1u << 30) - 1u;
+// Longest a tile waits for a predecessor before it reports a timeout.
+constexpr uint64_t LOOKBACK_TIMEOUT_NS = 2000000000ull;
+constexpr uint32_t LOOKBACK_MAX_POLLS = 1u << 24;
+
+// Buffers a pass can read or write.
+enum : uint32_t { BUF_IN = 0, BUF_TMP = 1, BUF_OUT = 2 };
+enum : uint32_t { MODE_PASSES = 0, MODE_FILL = 1 };
+
+// The plan the device makes for itself from the counts (no host round trip):
+// which digit groups need a pass, where each pass reads and writes, and
+// whether the whole key space is one count array rebuilt from cells.
+struct DevPlan {
+    uint32_t mode;
+    uint32_t passes_run;
+    uint32_t first_active;  // MAX_PASSES if none
+    uint32_t last_active;
+    uint32_t active[MAX_PASSES];
+    uint32_t src[MAX_PASSES];
+    uint32_t dst[MAX_PASSES];
+    uint32_t hist_done;           // CTAs of the counting kernel that finished
+    uint32_t fill_impossible;     // some key's cell is >= FILL_CELLS
+    uint32_t tile_counter[MAX_PASSES];
+};
+
+// What the last sort decided, kept in the context for diagnostics.
+struct DevInfo {
+    uint32_t mode;
+    uint32_t passes_run;
+};
+
+struct CodecParams {
+    uint64_t bias;  // fixed-point decimals: 10^D - 1
+};
+
+// ------------------------------------------------------------------ codecs
+// decode: input key -> cell (sets ok = false for a key outside its space)
+// encode: cell -> output key (the key rebuilt from its cell, Eq. 16)
+
+struct CodecU32 {
+    using In = uint32_t;
+    using Cell = uint32_t;
+    using Out = uint32_t;
+    __device__ static Cell decode(In k, const CodecParams&, bool&) { return k; }
+    __device__ static Out encode(Cell c, const CodecParams&) { return c; }
+};
+
+struct CodecU64 {
+    using In = uint64_t;
+    using Cell = uint64_t;
+    using Out = uint64_t;
+    __device__ static Cell decode(In k, const CodecParams&, bool&) { return k; }
+    __device__ static Out encode(Cell c, const CodecParams&) { return c; }
+};
+
+// Fixed-point decimal with D = int_digits + frac_digits digits: the cell of
+// v is v + (10^D - 1), a monotone map of [-(10^D-1), 10^D-1] onto
+// [0, 2*10^D - 2].  CellT = uint32_t when 2*10^D - 2 < 2^32 (D <= 9).
+template <typename CellT>
+struct CodecDec {
+    using In = int64_t;
+    using Cell = CellT;
+    using Out = int64_t;
+    __device__ static Cell decode(In v, const CodecParams& p, bool& ok) {
+        const int64_t b = (int64_t)p.bias;
+        if (v < -b || v > b) {
+            ok = false;
+            v = v < 0 ? -b : b;
+        }
+        return (Cell)(uint64_t)(v + b);
+    }
+    __device__ static Out encode(Cell c, const CodecParams& p) {
+        return (int64_t)(uint64_t)c - (int64_t)p.bias;
+    }
+};
+
+// ------------------------------------------------------------------ helpers
+
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Lanes of the warp holding the same 8-bit digit: one ballot per bit.
+__device__ __forceinline__ uint32_t match_digit(uint32_t d) {
+    uint32_t m = 0xffffffffu;
+#pragma unroll
+    for (int b = 0; b < RADIX_BITS; b++) {
+        const uint32_t bit = (d >> b) & 1u;
+        const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+        m &= bit ? bal : ~bal;
+    }
+    return m;
+}
+
+template <typename T>
+__device__ __forceinline__ uint32_t digit_of(T cell, uint32_t shift) {
+    return (uint32_t)(cell >> shift) & (RADIX - 1);
+}
+
+// Exclusive scan of one value per thread over a 256-thread block.
+// s_warp must hold WARPS words; *total receives the block sum.
+// Contains __syncthreads(); every thread of the block must call it.
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* s_warp,
+                                                         uint32_t* total) {
+    const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= (uint32_t)o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    uint32_t before = 0, sum = 0;
+#pragma unroll
+    for (int w = 0; w < WARPS; w++) {
+        const uint32_t s = s_warp[w];
+        before += (uint32_t)w < warp ? s : 0u;
+        sum += s;
+    }
+    __syncthreads();  // s_warp may be reused by the caller
+    *total = sum;
+    return before + x - v;
+}
+
+}  // namespace rs

@@ -1,0 +1,448 @@
+// rs_kernels.cuh -- the Recombinant Sort hot path as CUDA kernels (sm_103a).
+//
+//   count_kernel  the hashing cycle (§3.1, Eq. 1): one read of the keys
+//                 counts every key into the 256 cells of each digit group
+//                 (and, while every cell index stays below FILL_CELLS, into
+//                 one dense count array).  Its last CTA turns the counts into
+//                 raster-order cell offsets (the extraction cycle's cursor
+//                 overwrite_pos_at, §3.2) and the device-side plan.
+//   pass_kernel   one digit group: stable in-tile ranking with warp ballots,
+//                 a single-pass decoupled look-back exclusive scan across
+//                 tiles in input order, and a scatter staged through shared
+//                 memory so global writes coalesce.  Keys and payloads move
+//                 together.
+//   fill_kernel   keys only, one count array: write every occupied cell's
+//                 key, rebuilt from its coordinates (Eq. 16), count times.
+#pragma once
+
+#include <type_traits>
+
+#include "rs_device.cuh"
+
+namespace rs {
+
+struct CountArgs {
+    const void* keys_in;
+    uint64_t n;
+    uint32_t passes;        // digit groups of the cell index
+    uint32_t fill_allowed;  // keys-only call: the dense count array may be used
+    uint32_t in_is_out;     // keys_in == keys_out (an odd pass count is not allowed)
+    uint32_t pad_;
+    CodecParams prm;
+    DevPlan* plan;
+    uint32_t* hist;          // [passes][RADIX] counts
+    uint32_t* bin_offsets;   // [passes][RADIX] raster-order exclusive offsets
+    uint32_t* fill_hist;     // [FILL_CELLS]
+    uint32_t* fill_offsets;  // [FILL_CELLS + 1]
+    uint32_t* status;
+    DevInfo* info;
+};
+
+// ----------------------------------------------------------------------------
+// Hashing cycle: count every key into each digit group's 256 cells.
+
+template <class C>
+__device__ __forceinline__ void count_one(typename C::In key, const CountArgs& a,
+                                          uint32_t (*sh)[RADIX], uint32_t* sfill, bool& ok,
+                                          bool& big) {
+    const typename C::Cell cell = C::decode(key, a.prm, ok);
+    for (uint32_t p = 0; p < a.passes; p++) atomicAdd(&sh[p][digit_of(cell, p * RADIX_BITS)], 1u);
+    if (a.fill_allowed && !big) {
+        if (cell < (typename C::Cell)FILL_CELLS)
+            atomicAdd(&sfill[(uint32_t)cell], 1u);
+        else
+            big = true;
+    }
+}
+
+// The last CTA of count_kernel: offsets, trivial groups, routing.
+static __device__ void make_plan(const CountArgs& a, uint32_t* s_warp) {
+    __shared__ uint32_t s_trivial[MAX_PASSES];
+    const uint32_t t = threadIdx.x;
+    for (uint32_t p = 0; p < a.passes; p++) {
+        const uint32_t h = __ldcg(&a.hist[p * RADIX + t]);
+        uint32_t total;
+        const uint32_t excl = block_exclusive_scan(h, s_warp, &total);
+        a.bin_offsets[p * RADIX + t] = excl;
+        const int occupied = __syncthreads_count(h != 0);
+        if (t == 0) s_trivial[p] = occupied <= 1;  // every key in one cell: identity
+    }
+    const bool fill = a.fill_allowed && __ldcg(&a.plan->fill_impossible) == 0;
+    if (fill) {
+        // raster-order offsets of the dense count array: 16 cells per thread
+        uint32_t local[FILL_CELLS / BLOCK];
+        uint32_t sum = 0;
+#pragma unroll
+        for (int i = 0; i < (int)(FILL_CELLS / BLOCK); i++) {
+            local[i] = __ldcg(&a.fill_hist[t * (FILL_CELLS / BLOCK) + i]);
+            sum += local[i];
+        }
+        uint32_t total;
+        uint32_t run = block_exclusive_scan(sum, s_warp, &total);
+#pragma unroll
+        for (int i = 0; i < (int)(FILL_CELLS / BLOCK); i++) {
+            a.fill_offsets[t * (FILL_CELLS / BLOCK) + i] = run;
+            run += local[i];
+        }
+        if (t == BLOCK - 1) a.fill_offsets[FILL_CELLS] = run;
+    }
+    __syncthreads();
+    if (t == 0) {
+        DevPlan* P = a.plan;
+        uint32_t active[MAX_PASSES];
+        uint32_t m = 0;
+        for (uint32_t p = 0; p < a.passes; p++) {
+            active[p] = fill ? 0u : (s_trivial[p] ? 0u : 1u);
+            m += active[p];
+        }
+        if (!fill) {
+            // In place, every pass alternates buffers, so the pass count must
+            // be even; out of place, at least one pass must copy.  A trivial
+            // group is an identity permutation, so running one costs nothing
+            // in correctness.
+            const bool need_one_more = a.in_is_out ? (m & 1u) : (m == 0);
+            if (need_one_more) {
+                for (uint32_t p = 0; p < a.passes; p++)
+                    if (!active[p]) {
+                        active[p] = 1;
+                        m++;
+                        break;
+                    }
+            }
+        }
+        // Route: the last active pass writes OUT; going backwards the
+        // destinations alternate OUT, TMP, OUT, ...; the first reads IN.
+        uint32_t k = 0, prev_dst = BUF_IN;
+        P->first_active = MAX_PASSES;
+        P->last_active = MAX_PASSES;
+        for (uint32_t p = 0; p < a.passes; p++) {
+            P->active[p] = active[p];
+            if (!active[p]) continue;
+            const uint32_t from_end = m - 1 - k;
+            P->src[p] = prev_dst;
+            P->dst[p] = (from_end & 1u) ? BUF_TMP : BUF_OUT;
+            prev_dst = P->dst[p];
+            if (P->first_active == MAX_PASSES) P->first_active = p;
+            P->last_active = p;
+            k++;
+        }
+        P->passes_run = m;
+        P->mode = fill ? MODE_FILL : MODE_PASSES;
+        a.info->mode = P->mode;
+        a.info->passes_run = m;
+    }
+}
+
+template <class C>
+__global__ void __launch_bounds__(BLOCK) count_kernel(CountArgs a) {
+    using In = typename C::In;
+    __shared__ uint32_t sh[MAX_PASSES][RADIX];
+    __shared__ uint32_t sfill[FILL_CELLS];
+    __shared__ uint32_t s_warp[WARPS];
+    __shared__ uint32_t s_last;
+    const uint32_t t = threadIdx.x;
+    for (uint32_t i = t; i < MAX_PASSES * RADIX; i += BLOCK) (&sh[0][0])[i] = 0;
+    if (a.fill_allowed)
+        for (uint32_t i = t; i < FILL_CELLS; i += BLOCK) sfill[i] = 0;
+    __syncthreads();
+
+    const In* keys = static_cast<const In*>(a.keys_in);
+    bool ok = true;
+    bool big = a.fill_allowed ? (__ldcg(&a.plan->fill_impossible) != 0) : true;
+    // 16-byte vector body with a scalar head and tail.
+    constexpr uint32_t VEC = 16 / sizeof(In);
+    const uintptr_t addr = reinterpret_cast<uintptr_t>(keys);
+    uint64_t head = ((16 - (addr & 15)) & 15) / sizeof(In);
+    if (head > a.n) head = a.n;
+    const uint64_t nvec = (a.n - head) / VEC;
+    const uint64_t tail0 = head + nvec * VEC;
+    const uint64_t gtid = (uint64_t)blockIdx.x * BLOCK + t;
+    const uint64_t gsize = (uint64_t)gridDim.x * BLOCK;
+    if (gtid < head) count_one<C>(keys[gtid], a, sh, sfill, ok, big);
+    const uint4* vkeys = reinterpret_cast<const uint4*>(keys + head);
+    for (uint64_t v = gtid; v < nvec; v += gsize) {
+        const uint4 q = __ldg(&vkeys[v]);
+        const In* e = reinterpret_cast<const In*>(&q);
+#pragma unroll
+        for (uint32_t j = 0; j < VEC; j++) count_one<C>(e[j], a, sh, sfill, ok, big);
+    }
+    if (tail0 + gtid < a.n) count_one<C>(keys[tail0 + gtid], a, sh, sfill, ok, big);
+    if (!ok) atomicOr(a.status, STATUS_RANGE);
+    if (a.fill_allowed && big) a.plan->fill_impossible = 1;
+    __syncthreads();
+
+    for (uint32_t i = t; i < a.passes * RADIX; i += BLOCK) {
+        const uint32_t c = (&sh[0][0])[i];
+        if (c) atomicAdd(&a.hist[i], c);
+    }
+    if (a.fill_allowed && __ldcg(&a.plan->fill_impossible) == 0) {
+        for (uint32_t i = t; i < FILL_CELLS; i += BLOCK)
+            if (sfill[i]) atomicAdd(&a.fill_hist[i], sfill[i]);
+    }
+    __threadfence();
+    __syncthreads();
+    if (t == 0) s_last = atomicAdd(&a.plan->hist_done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    make_plan(a, s_warp);
+}
+
+// ----------------------------------------------------------------------------
+// One digit group: rank, look back, scatter.
+
+struct PassArgs {
+    const void* keys_in;
+    void* keys_tmp;
+    void* keys_out;
+    const void* vals_in;
+    void* vals_tmp;
+    void* vals_out;
+    uint64_t n;
+    uint32_t pass;
+    uint32_t shift;
+    CodecParams prm;
+    const DevPlan* plan;
+    const uint32_t* bin_offsets;  // this group's 256 raster-order offsets
+    uint32_t* lookback;           // [tiles][RADIX] for this pass
+    uint32_t* lookback_next;      // cleared here for the next pass
+    uint32_t* tile_counter;
+    uint32_t* status;
+};
+
+struct NoVal {};
+
+template <typename V>
+struct ValTraits {
+    static constexpr bool kPairs = true;
+};
+template <>
+struct ValTraits<NoVal> {
+    static constexpr bool kPairs = false;
+};
+
+template <typename Cell, typename V, int IPT>
+struct PassSmem {
+    static constexpr int TILE = BLOCK * IPT;
+    static constexpr size_t kKeys = sizeof(Cell) * TILE;
+    static constexpr size_t kVals = ValTraits<V>::kPairs ? sizeof(V) * TILE : 0;
+    static constexpr size_t kBytes = kKeys + kVals;
+};
+
+__device__ __forceinline__ const void* pick_src(const PassArgs& a, uint32_t b, bool vals) {
+    if (b == BUF_IN) return vals ? a.vals_in : a.keys_in;
+    if (b == BUF_TMP) return vals ? a.vals_tmp : a.keys_tmp;
+    return vals ? a.vals_out : a.keys_out;
+}
+__device__ __forceinline__ void* pick_dst(const PassArgs& a, uint32_t b, bool vals) {
+    if (b == BUF_TMP) return vals ? a.vals_tmp : a.keys_tmp;
+    return vals ? a.vals_out : a.keys_out;
+}
+
+template <class C, typename V, int IPT>
+__global__ void __launch_bounds__(BLOCK) pass_kernel(PassArgs a) {
+    using Cell = typename C::Cell;
+    using In = typename C::In;
+    using Out = typename C::Out;
+    constexpr bool kPairs = ValTraits<V>::kPairs;
+    constexpr int TILE = BLOCK * IPT;
+    using VS = typename std::conditional<kPairs, V, uint32_t>::type;  // storage type
+
+    __shared__ uint32_t wh[WARPS][RADIX];     // per-warp digit counters, then prefixes
+    __shared__ uint32_t s_bin_excl[RADIX];    // tile-local start of each cell
+    __shared__ uint32_t s_bin_global[RADIX];  // global position of tile-local index 0 per cell
+    __shared__ uint32_t s_warp[WARPS];
+    __shared__ uint32_t s_tile;
+    extern __shared__ __align__(16) unsigned char smem_dyn[];
+    Cell* s_keys = reinterpret_cast<Cell*>(smem_dyn);
+    VS* s_vals = reinterpret_cast<VS*>(smem_dyn + sizeof(Cell) * TILE);
+
+    const uint32_t t = threadIdx.x, lane = lane_id(), warp = t >> 5;
+
+    // The next pass's look-back rows are free once this pass started: clear
+    // one row per CTA (the grid has one CTA per tile).
+    a.lookback_next[(uint64_t)blockIdx.x * RADIX + t] = 0;
+
+    const DevPlan* P = a.plan;
+    if (P->mode != MODE_PASSES || !P->active[a.pass]) return;
+    const bool first = P->first_active == a.pass;
+    const bool last = P->last_active == a.pass;
+
+    if (t == 0) s_tile = atomicAdd(a.tile_counter, 1u);
+    for (uint32_t d = lane; d < RADIX; d += 32) wh[warp][d] = 0;
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const uint64_t tile_base = (uint64_t)tile * TILE;
+    const uint32_t valid = (uint32_t)min((uint64_t)TILE, a.n - tile_base);
+
+    // ---- load (warp-striped: warp w owns inputs [w*32*IPT, (w+1)*32*IPT)) ----
+    const uint64_t wbase = tile_base + (uint64_t)warp * 32 * IPT + lane;
+    Cell k[IPT];
+    VS v[IPT];
+    const void* ksrc = pick_src(a, P->src[a.pass], false);
+    if (first) {
+        const In* in = static_cast<const In*>(ksrc);
+        bool ok = true;
+#pragma unroll
+        for (int i = 0; i < IPT; i++) {
+            const uint64_t idx = wbase + (uint64_t)i * 32;
+            k[i] = idx < a.n ? C::decode(__ldcs(&in[idx]), a.prm, ok) : ~Cell(0);
+        }
+    } else {
+        const Cell* in = static_cast<const Cell*>(ksrc);
+#pragma unroll
+        for (int i = 0; i < IPT; i++) {
+            const uint64_t idx = wbase + (uint64_t)i * 32;
+            k[i] = idx < a.n ? __ldcs(&in[idx]) : ~Cell(0);
+        }
+    }
+    if constexpr (kPairs) {
+        const VS* vin = static_cast<const VS*>(pick_src(a, P->src[a.pass], true));
+#pragma unroll
+        for (int i = 0; i < IPT; i++) {
+            const uint64_t idx = wbase + (uint64_t)i * 32;
+            v[i] = idx < a.n ? __ldcs(&vin[idx]) : VS(0);
+        }
+    }
+
+    // ---- stable rank within the warp: items in input order (i, then lane) ----
+    uint32_t rank[IPT];
+    const uint32_t lt = lanemask_lt();
+#pragma unroll
+    for (int i = 0; i < IPT; i++) {
+        const uint32_t d = digit_of(k[i], a.shift);
+        const uint32_t peers = match_digit(d);
+        const uint32_t leader = 31 - __clz(peers);
+        uint32_t old = 0;
+        if (lane == leader) {
+            old = wh[warp][d];
+            wh[warp][d] = old + __popc(peers);
+        }
+        old = __shfl_sync(0xffffffffu, old, leader);
+        rank[i] = old + __popc(peers & lt);
+        __syncwarp();
+    }
+    __syncthreads();
+
+    // ---- per-cell tile counts, warp prefixes, publish, tile-local offsets ----
+    uint32_t run = 0;
+#pragma unroll
+    for (int w = 0; w < WARPS; w++) {
+        const uint32_t x = wh[w][t];
+        wh[w][t] = run;
+        run += x;
+    }
+    // padding items carry cell ~0 (digit 255) and sit after every real item
+    const uint32_t count = t == RADIX - 1 ? run - (TILE - valid) : run;
+    uint32_t* lb = a.lookback + (uint64_t)tile * RADIX;
+    st_relaxed(&lb[t], (tile == 0 ? LB_INCLUSIVE : LB_AGGREGATE) | count);
+    uint32_t tile_total;
+    const uint32_t excl = block_exclusive_scan(count, s_warp, &tile_total);
+    s_bin_excl[t] = excl;
+    __syncthreads();
+
+    // ---- scatter into shared memory in (cell, input) order ----
+#pragma unroll
+    for (int i = 0; i < IPT; i++) {
+        const uint32_t d = digit_of(k[i], a.shift);
+        const uint32_t pos = s_bin_excl[d] + wh[warp][d] + rank[i];
+        s_keys[pos] = k[i];
+        if constexpr (kPairs) s_vals[pos] = v[i];
+    }
+
+    // ---- decoupled look-back: this cell's count in all earlier tiles ----
+    uint32_t before = 0;
+    if (tile > 0) {
+        int64_t j = (int64_t)tile - 1;
+        const uint64_t t0 = global_ns();
+        uint32_t spins = 0;
+        while (true) {
+            const uint32_t s = ld_relaxed(&a.lookback[(uint64_t)j * RADIX + t]);
+            const uint32_t flag = s & ~LB_VALUE;
+            if (flag == 0) {
+                // bounded wait: by time, and by polls in case the timer stalls
+                if ((++spins & 63u) == 0 &&
+                    (global_ns() - t0 > LOOKBACK_TIMEOUT_NS || spins > LOOKBACK_MAX_POLLS)) {
+                    atomicOr(a.status, STATUS_TIMEOUT);
+                    break;  // give up; publish what we have so successors finish
+                }
+                continue;
+            }
+            before += s & LB_VALUE;
+            if (flag == LB_INCLUSIVE || j == 0) break;
+            --j;
+        }
+        st_relaxed(&lb[t], LB_INCLUSIVE | ((before + count) & LB_VALUE));
+    }
+    s_bin_global[t] = a.bin_offsets[t] + before - excl;
+    __syncthreads();
+
+    // ---- coalesced write-out: consecutive threads, consecutive positions ----
+    void* kdst = pick_dst(a, P->dst[a.pass], false);
+    VS* vdst = kPairs ? static_cast<VS*>(pick_dst(a, P->dst[a.pass], true)) : nullptr;
+    if (last) {
+        Out* out = static_cast<Out*>(kdst);
+        for (uint32_t j = t; j < valid; j += BLOCK) {
+            const Cell c = s_keys[j];
+            const uint32_t g = s_bin_global[digit_of(c, a.shift)] + j;
+            if (g >= a.n) continue;  // only after a timed-out wait
+            __stcs(&out[g], C::encode(c, a.prm));
+            if constexpr (kPairs) __stcs(&vdst[g], s_vals[j]);
+        }
+    } else {
+        Cell* out = static_cast<Cell*>(kdst);
+        for (uint32_t j = t; j < valid; j += BLOCK) {
+            const Cell c = s_keys[j];
+            const uint32_t g = s_bin_global[digit_of(c, a.shift)] + j;
+            if (g >= a.n) continue;  // only after a timed-out wait
+            out[g] = c;
+            if constexpr (kPairs) vdst[g] = s_vals[j];
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Keys only, one count array: the extraction cycle writes each cell's key
+// (Eq. 16) once per count.  Warp-strided output positions coalesce.
+
+struct FillArgs {
+    void* keys_out;
+    uint64_t n;
+    CodecParams prm;
+    const DevPlan* plan;
+    const uint32_t* fill_offsets;  // [FILL_CELLS + 1]
+};
+
+constexpr int FILL_IPT = 16;
+
+template <class C>
+__global__ void __launch_bounds__(BLOCK) fill_kernel(FillArgs a) {
+    using Out = typename C::Out;
+    using Cell = typename C::Cell;
+    if (a.plan->mode != MODE_FILL) return;
+    const uint32_t lane = lane_id();
+    const uint64_t warp_g = ((uint64_t)blockIdx.x * BLOCK + threadIdx.x) >> 5;
+    const uint64_t base = warp_g * 32 * FILL_IPT;
+    if (base >= a.n) return;
+    Out* out = static_cast<Out*>(a.keys_out);
+    const uint32_t* off = a.fill_offsets;
+    // the cell of output position j: the last cell whose offset is <= j
+    // (empty cells share their successor's offset and are stepped over)
+    uint64_t j = base + lane;
+    uint32_t lo = 0, hi = FILL_CELLS;
+    if (j < a.n) {
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (__ldg(&off[mid]) <= j) lo = mid; else hi = mid;
+        }
+    }
+    uint32_t cell = lo;
+#pragma unroll 4
+    for (int i = 0; i < FILL_IPT; i++, j += 32) {
+        if (j >= a.n) break;
+        while (cell + 1 < FILL_CELLS && __ldg(&off[cell + 1]) <= j) cell++;
+        __stcs(&out[j], C::encode((Cell)cell, a.prm));
+    }
+}
+
+}  // namespace rs

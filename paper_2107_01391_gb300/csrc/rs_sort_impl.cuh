@@ -1,0 +1,170 @@
+// rs_sort_impl.cuh -- workspace layout and launch sequence of one sort.
+//
+// Launch sequence (all on the caller's stream, no host synchronisation):
+//   1. cudaMemsetAsync: device plan, counters, counts, look-back buffer 0
+//   2. count_kernel   hashing cycle + device-side plan (last CTA)
+//   3. fill_kernel    keys-only single count array (exits at once otherwise)
+//   4. pass_kernel x passes_total, least significant digit group first
+//      (each exits at once when the plan marks its group trivial)
+#pragma once
+
+#include <algorithm>
+#include <cstring>
+
+#include "rs_ctx.hpp"
+#include "rs_kernels.cuh"
+
+namespace rs {
+
+inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+template <class C>
+constexpr int ipt_for() {
+    return sizeof(typename C::Cell) == 4 ? 16 : 12;
+}
+
+struct Layout {
+    size_t plan, hist, bin_offsets, fill_hist, fill_offsets, lookback0, lookback1;
+    size_t keys_tmp, vals_tmp, total, memset_bytes;
+    uint64_t tiles;
+};
+
+inline Layout make_layout(size_t n, uint32_t passes, int tile, size_t cell_bytes,
+                          size_t val_bytes) {
+    Layout L{};
+    L.tiles = (n + tile - 1) / tile;
+    size_t at = 0;
+    L.plan = at;          at += align_up(sizeof(DevPlan));
+    L.hist = at;          at += align_up(sizeof(uint32_t) * MAX_PASSES * RADIX);
+    L.fill_hist = at;     at += align_up(sizeof(uint32_t) * FILL_CELLS);
+    L.lookback0 = at;     at += align_up(sizeof(uint32_t) * RADIX * std::max<uint64_t>(L.tiles, 1));
+    L.memset_bytes = at;  // everything above starts at zero
+    L.lookback1 = at;     at += align_up(sizeof(uint32_t) * RADIX * std::max<uint64_t>(L.tiles, 1));
+    L.bin_offsets = at;   at += align_up(sizeof(uint32_t) * MAX_PASSES * RADIX);
+    L.fill_offsets = at;  at += align_up(sizeof(uint32_t) * (FILL_CELLS + 1));
+    L.keys_tmp = at;      at += align_up(cell_bytes * std::max<size_t>(n, 1));
+    L.vals_tmp = at;      at += align_up(val_bytes * std::max<size_t>(n, 1));
+    (void)passes;
+    L.total = at;
+    return L;
+}
+
+inline int count_grid(size_t n, int sms) {
+    // ~16 vector loads per thread, at most 4 CTAs per SM
+    const size_t per_cta = (size_t)BLOCK * 64;
+    size_t g = (n + per_cta - 1) / per_cta;
+    g = std::max<size_t>(1, std::min<size_t>(g, (size_t)sms * 4));
+    return (int)g;
+}
+
+inline int sm_count(int device) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || v <= 0)
+        v = 152;
+    return v;
+}
+
+// One sort: keys_in (C::In) -> keys_out (C::Out), values V (NoVal = keys only).
+template <class C, typename V>
+rs_status run_sort(rs_ctx* ctx, const void* keys_in, void* keys_out, const void* vals_in,
+                   void* vals_out, size_t n, CodecParams prm, uint32_t cell_bits, void* temp,
+                   size_t* temp_bytes, cudaStream_t stream) {
+    using Cell = typename C::Cell;
+    constexpr bool kPairs = ValTraits<V>::kPairs;
+    constexpr int IPT = ipt_for<C>();
+    constexpr int TILE = BLOCK * IPT;
+    const uint32_t passes = std::max<uint32_t>(1, (cell_bits + RADIX_BITS - 1) / RADIX_BITS);
+    const size_t vbytes = kPairs ? sizeof(V) : 0;
+    const Layout L = make_layout(n, passes, TILE, sizeof(Cell), vbytes);
+
+    if (!temp_bytes) return RS_ERR_INVALID;
+    if (!temp) {
+        *temp_bytes = L.total;
+        return RS_OK;
+    }
+    if (*temp_bytes < L.total) return RS_ERR_TEMP_TOO_SMALL;
+    if (reinterpret_cast<uintptr_t>(temp) % 256) return RS_ERR_INVALID;
+    if (n == 0) return RS_OK;
+
+    DeviceGuard dg(ctx->device);
+    if (!dg.ok) return RS_ERR_CUDA;
+    unsigned char* T = static_cast<unsigned char*>(temp);
+    DevPlan* plan = reinterpret_cast<DevPlan*>(T + L.plan);
+    uint32_t* hist = reinterpret_cast<uint32_t*>(T + L.hist);
+    uint32_t* bin_offsets = reinterpret_cast<uint32_t*>(T + L.bin_offsets);
+    uint32_t* fill_hist = reinterpret_cast<uint32_t*>(T + L.fill_hist);
+    uint32_t* fill_offsets = reinterpret_cast<uint32_t*>(T + L.fill_offsets);
+    uint32_t* lb[2] = {reinterpret_cast<uint32_t*>(T + L.lookback0),
+                       reinterpret_cast<uint32_t*>(T + L.lookback1)};
+
+    if (cudaMemsetAsync(T, 0, L.memset_bytes, stream) != cudaSuccess) return RS_ERR_CUDA;
+
+    const bool fill_allowed = !kPairs;
+    {
+        CountArgs a{};
+        a.keys_in = keys_in;
+        a.n = n;
+        a.passes = passes;
+        a.fill_allowed = fill_allowed;
+        a.in_is_out = keys_in == keys_out;
+        a.prm = prm;
+        a.plan = plan;
+        a.hist = hist;
+        a.bin_offsets = bin_offsets;
+        a.fill_hist = fill_hist;
+        a.fill_offsets = fill_offsets;
+        a.status = ctx->d_status;
+        a.info = static_cast<DevInfo*>(ctx->d_info);
+        LaunchTimer lt(ctx, KC_HIST, stream);
+        count_kernel<C><<<count_grid(n, sm_count(ctx->device)), BLOCK, 0, stream>>>(a);
+    }
+    if (fill_allowed) {
+        FillArgs f{};
+        f.keys_out = keys_out;
+        f.n = n;
+        f.prm = prm;
+        f.plan = plan;
+        f.fill_offsets = fill_offsets;
+        const size_t per_cta = (size_t)BLOCK * FILL_IPT;
+        const unsigned grid = (unsigned)((n + per_cta - 1) / per_cta);
+        LaunchTimer lt(ctx, KC_FILL, stream);
+        fill_kernel<C><<<grid, BLOCK, 0, stream>>>(f);
+    }
+    using Smem = PassSmem<Cell, V, IPT>;
+    auto kern = pass_kernel<C, V, IPT>;
+    if (Smem::kBytes > 48 * 1024) {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)Smem::kBytes) != cudaSuccess)
+            return RS_ERR_CUDA;
+    }
+    for (uint32_t p = 0; p < passes; p++) {
+        PassArgs a{};
+        a.keys_in = keys_in;
+        a.keys_tmp = T + L.keys_tmp;
+        a.keys_out = keys_out;
+        a.vals_in = vals_in;
+        a.vals_tmp = kPairs ? (void*)(T + L.vals_tmp) : nullptr;
+        a.vals_out = vals_out;
+        a.n = n;
+        a.pass = p;
+        a.shift = p * RADIX_BITS;
+        a.prm = prm;
+        a.plan = plan;
+        a.bin_offsets = bin_offsets + p * RADIX;
+        a.lookback = lb[p & 1];
+        a.lookback_next = lb[(p + 1) & 1];
+        a.tile_counter = &plan->tile_counter[p];
+        a.status = ctx->d_status;
+        LaunchTimer lt(ctx, KC_PASS, stream);
+        kern<<<(unsigned)L.tiles, BLOCK, Smem::kBytes, stream>>>(a);
+    }
+    ctx->last_passes_total = passes;
+    ctx->last_tiles = (uint32_t)L.tiles;
+    return cudaGetLastError() == cudaSuccess ? RS_OK : RS_ERR_CUDA;
+}
+
+#define RS_DECLARE_SORT(C, V)                                                                  \
+    template rs_status run_sort<C, V>(rs_ctx*, const void*, void*, const void*, void*, size_t, \
+                                      CodecParams, uint32_t, void*, size_t*, cudaStream_t);
+
+}  // namespace rs

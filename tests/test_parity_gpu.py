@@ -1,0 +1,266 @@
+"""Parity of the CUDA path against the CPU oracle, element by element.
+
+Sizes span several tiles (4096 keys for 32-bit cells, 3072 for 64-bit) with
+ragged tails; every comparison is bit-exact (keys, and payload order for
+pairs).  All calls go through the C ABI via the thin binding.
+"""
+import numpy as np
+import pytest
+import torch
+
+from gpu_util import from_dev, require_gpu, to_dev
+from paper_2107_01391_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+SIZES_U32 = [1, 2, 3, 31, 4095, 4096, 4097, 3 * 4096 + 17, 100_003]
+
+
+@pytest.fixture(scope="module")
+def rs():
+    require_gpu()
+    from paper_2107_01391_gb300 import build, binding
+    build.build()
+    return binding
+
+
+@pytest.fixture(scope="module")
+def ctx(rs):
+    c = rs.Context(0)
+    yield c
+    c.close()
+
+
+def _sort_u32(rs, ctx, keys, inplace=False):
+    d = to_dev(keys)
+    out = rs.rs_sort_u32(d, d if inplace else None, ctx=ctx)
+    ctx.check()
+    return from_dev(out, np.uint32)
+
+
+# --------------------------------------------------------------- keys only
+
+
+def test_digits3_fill_path_full_size(rs, ctx, oracle):
+    keys = W.digits3(1 << 20)
+    ref, _, st = oracle.sort_u32(keys)
+    assert st.regenerated  # the oracle also rebuilt keys from cells (Eq. 16)
+    got = _sort_u32(rs, ctx, keys)
+    assert np.array_equal(got, ref)
+    assert ctx.last_plan()["mode"] == "fill"
+
+
+@pytest.mark.parametrize("n", SIZES_U32)
+def test_digits3_small(rs, ctx, oracle, n):
+    keys = W.digits3(n, seed_extra=n)
+    ref, _, _ = oracle.sort_u32(keys)
+    assert np.array_equal(_sort_u32(rs, ctx, keys), ref)
+
+
+@pytest.mark.parametrize("n", SIZES_U32)
+def test_u32_uniform_keys(rs, ctx, oracle, n):
+    keys = W.u32_keys(n, "uniform", seed_extra=n)
+    ref, _, _ = oracle.sort_u32(keys)
+    assert np.array_equal(_sort_u32(rs, ctx, keys), ref)
+    assert ctx.last_plan()["mode"] == "passes" or n < 3
+
+
+@pytest.mark.parametrize("dist", ["zipf", "presorted"])
+def test_u32_skewed_keys(rs, ctx, oracle, dist):
+    keys = W.u32_keys(200_001, dist)
+    ref, _, _ = oracle.sort_u32(keys)
+    assert np.array_equal(_sort_u32(rs, ctx, keys), ref)
+
+
+@pytest.mark.parametrize("inplace", [False, True])
+@pytest.mark.parametrize("shape", ["one_group", "two_groups", "all_equal", "small_range_big"])
+def test_u32_trivial_groups_and_in_place(rs, ctx, oracle, inplace, shape):
+    rng = np.random.default_rng(17)
+    n = 50_000
+    if shape == "one_group":      # only bits 8..15 vary: a single active pass
+        keys = (rng.integers(0, 256, n) << 8).astype(np.uint32)
+    elif shape == "two_groups":   # bits 0..7 and 24..31 vary
+        keys = (rng.integers(0, 256, n) | (rng.integers(0, 256, n) << 24)).astype(np.uint32)
+    elif shape == "all_equal":
+        keys = np.full(n, 0xDEADBEEF, np.uint32)
+    else:                         # every key >= RS_FILL_CELLS but in a narrow range
+        keys = rng.integers(5000, 5100, n).astype(np.uint32)
+    ref, _, _ = oracle.sort_u32(keys)
+    assert np.array_equal(_sort_u32(rs, ctx, keys, inplace=inplace), ref)
+
+
+def test_u32_extremes(rs, ctx, oracle):
+    keys = np.array([0xFFFFFFFF, 0, 1, 0xFFFFFFFE, 0xFFFFFFFF, 0, 0x80000000] * 1000, np.uint32)
+    ref, _, _ = oracle.sort_u32(keys)
+    assert np.array_equal(_sort_u32(rs, ctx, keys), ref)
+
+
+def test_empty(rs, ctx):
+    d = torch.empty(0, dtype=torch.int32, device="cuda")
+    out = rs.rs_sort_u32(d, ctx=ctx)
+    ctx.check()
+    assert out.numel() == 0
+
+
+@pytest.mark.parametrize("n", [1, 3071, 3072, 3073, 70_001])
+def test_u64_keys(rs, ctx, oracle, n):
+    keys = W.u64_keys(n, seed_extra=n)
+    ref, _, _ = oracle.sort_u64(keys)
+    d = to_dev(keys)
+    out = rs.rs_sort_u64(d, ctx=ctx)
+    ctx.check()
+    assert np.array_equal(from_dev(out, np.uint64), ref)
+
+
+# --------------------------------------------------------------- decimals
+
+
+@pytest.mark.parametrize("n", [1, 4097, 150_001])
+def test_fixed_decimal_6_3(rs, ctx, oracle, n):
+    keys = W.decimals(n, 6, 3, seed_extra=n)
+    ref, _, _ = oracle.sort_fixed_decimal(keys, 6, 3)
+    out = rs.rs_sort_fixed_decimal(to_dev(keys), 6, 3, ctx=ctx)
+    ctx.check()
+    assert np.array_equal(from_dev(out, np.int64), ref)
+
+
+@pytest.mark.parametrize("lo,hi,cd", [(1, 10, 0), (1, 10, 1), (1, 10, 2), (1, 100, 0), (1, 100, 1)])
+def test_fixed_decimal_table1_cases(rs, ctx, oracle, lo, hi, cd):
+    # the paper's five data cases (Table 1) at GPU scale: one count array,
+    # output rebuilt from cells
+    rng = np.random.default_rng(cd + hi)
+    keys = rng.integers(lo * 10**cd, hi * 10**cd, 1 << 18).astype(np.int64)
+    int_digits = len(str(hi - 1))
+    ref, _, st = oracle.sort_fixed_decimal(keys, int_digits, cd)
+    out = rs.rs_sort_fixed_decimal(to_dev(keys), int_digits, cd, ctx=ctx)
+    ctx.check()
+    assert np.array_equal(from_dev(out, np.int64), ref)
+    assert ctx.last_plan()["mode"] == "fill"
+
+
+def test_fixed_decimal_example1(rs, ctx, oracle):
+    keys = np.array([45, 3, 23, 88, 70, 92, 45, 43, 80, 32], np.int64)
+    out = rs.rs_sort_fixed_decimal(to_dev(keys), 1, 1, ctx=ctx)
+    ctx.check()
+    assert from_dev(out, np.int64).tolist() == [3, 23, 32, 43, 45, 45, 70, 80, 88, 92]
+
+
+def test_fixed_decimal_signed_mixed_and_in_place(rs, ctx, oracle):
+    rng = np.random.default_rng(5)
+    keys = rng.integers(-(10**12) + 1, 10**12, 60_000).astype(np.int64)
+    keys[:4] = [-(10**12) + 1, 10**12 - 1, 0, -1]
+    ref, _, _ = oracle.sort_fixed_decimal(keys, 10, 2)
+    d = to_dev(keys)
+    rs.rs_sort_fixed_decimal(d, 10, 2, out=d, ctx=ctx)
+    ctx.check()
+    assert np.array_equal(from_dev(d, np.int64), ref)
+
+
+def test_fixed_decimal_range_error(rs, ctx):
+    keys = np.array([1, 2, 10**9, 3] * 100, np.int64)  # 10^9 needs 10 digits
+    rs.rs_sort_fixed_decimal(to_dev(keys), 6, 3, ctx=ctx)
+    assert ctx.status(True) == rs.RS_ERR_RANGE
+    assert ctx.status(True) == rs.RS_OK  # the status word was cleared
+
+
+# --------------------------------------------------------------- pairs
+
+
+@pytest.mark.parametrize("dist", ["uniform", "zipf", "presorted"])
+@pytest.mark.parametrize("n", [4097, 1_000_003])
+def test_u32_pairs(rs, ctx, oracle, dist, n):
+    keys, vals = W.u32_pairs(n, dist, seed_extra=n)
+    ref_k, ref_perm, _ = oracle.sort_u32(keys)
+    ko, vo = rs.rs_sort_pairs(to_dev(keys), to_dev(vals), ctx=ctx)
+    ctx.check()
+    assert np.array_equal(from_dev(ko, np.uint32), ref_k)
+    assert np.array_equal(from_dev(vo, np.uint32), ref_perm.astype(np.uint32))
+
+
+@pytest.mark.parametrize("inplace", [False, True])
+def test_u32_pairs_u64_values(rs, ctx, oracle, inplace):
+    rng = np.random.default_rng(3)
+    keys = rng.integers(0, 1000, 77_777).astype(np.uint32)  # many ties; pairs never fill
+    vals = rng.integers(0, 2**63, keys.size).astype(np.int64)
+    ref_k, perm, _ = oracle.sort_u32(keys)
+    dk, dv = to_dev(keys), to_dev(vals)
+    if inplace:
+        rs.rs_sort_pairs(dk, dv, dk, dv, ctx=ctx)
+        ko, vo = dk, dv
+    else:
+        ko, vo = rs.rs_sort_pairs(dk, dv, ctx=ctx)
+    ctx.check()
+    assert np.array_equal(from_dev(ko, np.uint32), ref_k)
+    assert np.array_equal(from_dev(vo, np.int64), vals[perm.astype(np.int64)])
+
+
+def test_u64_pairs(rs, ctx, oracle):
+    keys = W.u64_keys(40_000)
+    keys[::3] = keys[5]
+    vals = np.arange(keys.size, dtype=np.uint32)
+    ref_k, perm, _ = oracle.sort_u64(keys)
+    ko, vo = rs.rs_sort_pairs(to_dev(keys), to_dev(vals), ctx=ctx)
+    ctx.check()
+    assert np.array_equal(from_dev(ko, np.uint64), ref_k)
+    assert np.array_equal(from_dev(vo, np.uint32), perm.astype(np.uint32))
+
+
+def test_decimal_pairs(rs, ctx, oracle):
+    keys = W.decimals(123_457, 6, 3)
+    vals = np.arange(keys.size, dtype=np.uint32)
+    ref_k, perm, _ = oracle.sort_fixed_decimal(keys, 6, 3)
+    ko, vo = rs.rs_sort_pairs(to_dev(keys), to_dev(vals), decimal=(6, 3), ctx=ctx)
+    ctx.check()
+    assert np.array_equal(from_dev(ko, np.int64), ref_k)
+    assert np.array_equal(from_dev(vo, np.uint32), perm.astype(np.uint32))
+
+
+# --------------------------------------------------------------- full size
+
+
+def _check_stable_sort_properties(keys_in, keys_out, vals_out):
+    """On the device: output non-decreasing, payload a permutation, keys follow
+    their payloads, equal keys keep input order.  Together these determine
+    the stable sort uniquely."""
+    n = keys_in.numel()
+    ki = keys_in.to(torch.int64) & 0xFFFFFFFF
+    ko = keys_out.to(torch.int64) & 0xFFFFFFFF
+    v = vals_out.to(torch.int64) & 0xFFFFFFFF
+    assert bool((ko[1:] >= ko[:-1]).all())
+    seen = torch.zeros(n, dtype=torch.int32, device=keys_in.device)
+    seen.index_fill_(0, v, 1)
+    assert int(seen.sum()) == n
+    assert bool((ki[v] == ko).all())
+    same = ko[1:] == ko[:-1]
+    assert bool((v[1:][same] > v[:-1][same]).all())
+
+
+@pytest.mark.parametrize("dist", ["uniform", "zipf", "presorted"])
+def test_u32_pairs_full_size(rs, ctx, oracle, dist):
+    n = 1 << 28
+    keys, vals = W.u32_pairs(n, dist)
+    dk, dv = to_dev(keys), to_dev(vals)
+    ko, vo = rs.rs_sort_pairs(dk, dv, ctx=ctx)
+    ctx.check()
+    _check_stable_sort_properties(dk, ko, vo)
+    # sampled outputs against the plain definition of the stable rank
+    rng = np.random.default_rng(99)
+    ko_h, vo_h = from_dev(ko, np.uint32), from_dev(vo, np.uint32)
+    for i in rng.integers(0, n, 6):
+        r = oracle.stable_rank(keys, int(i))
+        assert ko_h[r] == keys[i] and vo_h[r] == i
+    del dk, dv, ko, vo
+    torch.cuda.empty_cache()
+
+
+def test_timing_and_launch_count(rs, ctx):
+    keys = to_dev(W.u32_keys(1 << 20))
+    ctx.set_timing(True)
+    ctx.reset_timing()
+    before = ctx.launch_count()
+    rs.rs_sort_u32(keys, ctx=ctx)
+    ctx.check()
+    ms, launches = ctx.kernel_time("pass")
+    assert launches == 4 and ms > 0
+    assert ctx.launch_count() - before == 6  # count + fill + 4 passes
+    ctx.set_timing(False)
