@@ -47,6 +47,10 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--dists", default="uniform,zipf,presorted")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    # smaller arrays for ncu captures only; a line printed with --log2n != 28
+    # is not a benchmark result
+    ap.add_argument("--log2n", type=int, default=28)
     return ap.parse_args()
 
 
@@ -210,7 +214,7 @@ def run_ours(args):
     build.build()
     ctx = binding.Context(local)
     stream = torch.cuda.current_stream()
-    n = N_KEYS
+    n = 1 << args.log2n
     hbm_peak, peak_kind = peaks()
     dists = [d for d in args.dists.split(",") if d]
 
@@ -354,7 +358,8 @@ def run_ours(args):
                       "pass_ms_avg": r["pass_ms_avg"], "count_ms_avg": r["count_ms_avg"],
                       "passes_run": r["passes_run"]} for d, r in results.items()},
         "e2e": e2e,
-        "cpu_baseline": cpu_baseline(ORACLE_SAMPLE) if world == 1 else None,
+        "cpu_baseline": (cpu_baseline(ORACLE_SAMPLE)
+                         if world == 1 and not args.no_cpu_baseline else None),
     }
     print(json.dumps(line), flush=True)
     if world > 1:

@@ -132,10 +132,14 @@ rs_status run_sort(rs_ctx* ctx, const void* keys_in, void* keys_out, const void*
     }
     using Smem = PassSmem<Cell, V, IPT>;
     auto kern = pass_kernel<C, V, IPT>;
-    if (Smem::kBytes > 48 * 1024) {
+    // static + dynamic shared memory may exceed the 48 KB default: opt in
+    // once per device for this instantiation
+    static bool smem_set[64] = {};
+    if (ctx->device < 64 && !smem_set[ctx->device]) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)Smem::kBytes) != cudaSuccess)
             return RS_ERR_CUDA;
+        smem_set[ctx->device] = true;
     }
     for (uint32_t p = 0; p < passes; p++) {
         PassArgs a{};
