@@ -129,6 +129,39 @@ rs_status rs_sort_pairs(rs_ctx* ctx, rs_key_type kt, const void* keys_in, void* 
                         const rs_key_params* params, void* temp, size_t* temp_bytes,
                         rs_stream_t stream);
 
+/* ------------------------------------------------------- no allocation */
+
+/* The paper has no counterpart to this call; it exists for callers that
+ * cannot allocate device memory when they sort.  cudaFree waits for the
+ * whole device and cudaMalloc can stall, which a latency-bound loop cannot
+ * afford, and code that runs inside another framework's memory budget (a
+ * plugin or a server that owns every device byte through its own pool) has
+ * no allocator it may call and no workspace to pass.
+ *
+ * rs_sort_u32_noalloc sorts n uint32 keys exactly as rs_sort_u32 does (same
+ * kernels, same stable result) but needs no context and no workspace: its
+ * workspace is a fixed RS_NOALLOC_SCRATCH_BYTES device array inside the
+ * library, which every GPU that loads the library holds until the process
+ * exits.  It allocates nothing.
+ *   keys_in, keys_out  device arrays of n keys (keys_out may equal keys_in);
+ *   n                  at most RS_NOALLOC_MAX_N, else RS_ERR_TEMP_TOO_SMALL
+ *                      and nothing is launched;
+ *   status             optional device word (NULL allowed): device-detected
+ *                      errors are OR-ed into it (value 2 = a look-back
+ *                      wait timed out), so the caller can check it after
+ *                      the stream finishes;
+ *   stream             the work is enqueued on it; the call does not wait.
+ * The call runs on the calling thread's current CUDA device.  Its first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture begins.  All calls on a device
+ * share the one array and each clears what must start at zero, so calls whose
+ * work overlaps on the GPU (concurrent streams, or host threads without
+ * ordering between them) race and must be serialised by the caller. */
+#define RS_NOALLOC_MAX_N ((size_t)1 << 20)
+#define RS_NOALLOC_SCRATCH_BYTES ((size_t)5 << 20)
+rs_status rs_sort_u32_noalloc(const uint32_t* keys_in, uint32_t* keys_out, size_t n,
+                              uint32_t* status, rs_stream_t stream);
+
 /* ------------------------------------------------------------ diagnostics */
 
 /* What the device-side plan of the most recent sort on this context chose

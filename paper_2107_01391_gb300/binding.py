@@ -300,5 +300,31 @@ def workspace_bytes(fn_name: str, n: int, **kw) -> int:
     return need.value
 
 
+def rs_sort_u32_noalloc(keys: torch.Tensor, out: torch.Tensor | None = None,
+                        status: torch.Tensor | None = None, *, stream=None) -> torch.Tensor:
+    """The uint32 keys-only sort whose workspace is built into the library.
+
+    For callers that cannot allocate device memory while sorting: the C call
+    allocates nothing (this wrapper only allocates ``out`` when it is not
+    given).  At most ``RS_NOALLOC_MAX_N`` keys.  ``status`` is an optional
+    one-element int32 CUDA tensor that collects device-side error bits.
+    Calls whose work overlaps on the GPU share one built-in workspace and race.
+    """
+    L = lib()
+    fn = L.rs_sort_u32_noalloc
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                   ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    _cuda(keys, "keys", 4, U32_DTYPES)
+    out = torch.empty_like(keys) if out is None else _cuda(out, "out", 4, U32_DTYPES)
+    st = _ptr(status) if status is not None else ctypes.c_void_p(0)
+    _check(fn(_ptr(keys), _ptr(out), keys.numel(), st, _stream(keys, stream)),
+           "rs_sort_u32_noalloc")
+    return out
+
+
+RS_NOALLOC_MAX_N = 1 << 20
+
+
 def version() -> str:
     return lib().rs_version().decode()
