@@ -129,6 +129,24 @@ rs_status rs_sort_pairs(rs_ctx* ctx, rs_key_type kt, const void* keys_in, void* 
                         const rs_key_params* params, void* temp, size_t* temp_bytes,
                         rs_stream_t stream);
 
+/* Stable sort of n byte strings: string i is chars[offsets[i] ..
+ * offsets[i+1]).  The paper's reading for strings (Table 2 claims them, §3
+ * gives no algorithm): one dimension of the count space per character
+ * position, with a padding symbol below every byte past a string's end, so
+ * the order is unsigned-byte lexicographic with a proper prefix first.
+ *   chars     device bytes; must cover chars[0 .. offsets[n]);
+ *   offsets   device uint32_t[n+1], non-decreasing;
+ *   max_len   1..RS_MAX_STRING_LEN, an upper bound on every length;
+ *   perm_out  device uint32_t[n]: perm_out[j] = input index of the j-th
+ *             smallest string (equal strings keep input order).
+ * A string longer than max_len, or offsets that decrease or pass offsets[n],
+ * raise RS_ERR_RANGE (device-detected); such strings are cut to fit and the
+ * output is unspecified. */
+#define RS_MAX_STRING_LEN 1024u
+rs_status rs_sort_strings(rs_ctx* ctx, const uint8_t* chars, const uint32_t* offsets, size_t n,
+                          uint32_t max_len, uint32_t* perm_out, void* temp, size_t* temp_bytes,
+                          rs_stream_t stream);
+
 /* ------------------------------------------------------- no allocation */
 
 /* The paper has no counterpart to this call; it exists for callers that
@@ -177,7 +195,9 @@ typedef struct rs_plan_info {
 rs_status rs_ctx_last_plan(rs_ctx* ctx, rs_plan_info* info);
 
 /* Per-kernel timing with CUDA events recorded on the launching stream around
- * every launch (off by default).  Kernel classes: "hist", "pass", "fill".
+ * every launch (off by default).  Kernel classes: "hist" (counting), "pass"
+ * (digit-group passes), "fill" (rebuild from cells), "pack" (string alphabet
+ * and packing), "seg" (segmented sort).
  * rs_ctx_kernel_time() synchronises, sums the elapsed time of every launch
  * of that class since timing was enabled or last reset, and returns it with
  * the launch count.  At most 65536 launches per class are kept. */

@@ -300,6 +300,44 @@ def workspace_bytes(fn_name: str, n: int, **kw) -> int:
     return need.value
 
 
+RS_MAX_STRING_LEN = 1024
+
+
+def rs_sort_strings(chars: torch.Tensor, offsets: torch.Tensor, max_len: int,
+                    perm_out: torch.Tensor | None = None, *, ctx: Context | None = None,
+                    stream=None, temp: torch.Tensor | None = None) -> torch.Tensor:
+    """Stable sort of byte strings; returns perm (int32 tensor holding uint32
+    indices): perm[j] is the input index of the j-th smallest string.
+
+    String i is ``chars[offsets[i]:offsets[i+1]]``; ``offsets`` has n+1
+    entries (int32/uint32 bits), ``chars`` is uint8.
+    """
+    _cuda(chars, "chars", 1, (torch.uint8,))
+    _cuda(offsets, "offsets", 4, U32_DTYPES)
+    n = offsets.numel() - 1
+    if n < 0:
+        raise ValueError("offsets needs n+1 entries")
+    perm_out = (torch.empty(n, dtype=torch.int32, device=offsets.device) if perm_out is None
+                else _cuda(perm_out, "perm_out", 4, U32_DTYPES))
+    ctx = ctx or default_context(offsets.device.index)
+    L = lib()
+    fn = L.rs_sort_strings
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                   ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
+                   ctypes.POINTER(ctypes.c_size_t), ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    s = _stream(offsets, stream)
+    cptr = ctypes.c_void_p(chars.data_ptr()) if chars.numel() else ctypes.c_void_p(
+        offsets.data_ptr())  # any valid device address; no byte is read when empty
+
+    def call(t, b):
+        return fn(ctx.handle, cptr, _ptr(offsets), n, max_len, _ptr(perm_out), t, b, s)
+
+    temp, tb = _workspace(call, offsets.device, temp)
+    _check(call(_ptr(temp), ctypes.byref(tb)), "rs_sort_strings")
+    return perm_out
+
+
 def rs_sort_u32_noalloc(keys: torch.Tensor, out: torch.Tensor | None = None,
                         status: torch.Tensor | None = None, *, stream=None) -> torch.Tensor:
     """The uint32 keys-only sort whose workspace is built into the library.

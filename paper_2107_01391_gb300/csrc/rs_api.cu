@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 
 #include "../../include/rs.h"
@@ -16,7 +17,7 @@
 namespace rs {
 template <class C, typename V>
 rs_status run_sort(rs_ctx*, const void*, void*, const void*, void*, size_t, CodecParams, uint32_t,
-                   void*, size_t*, cudaStream_t);
+                   void*, size_t*, cudaStream_t, const uint32_t* skip = nullptr);
 }  // namespace rs
 
 using namespace rs;
@@ -103,6 +104,8 @@ rs_status rs_ctx_create(rs_ctx** ctx, int device) {
         return RS_ERR_INVALID;
     rs_ctx* c = new rs_ctx();
     c->device = device;
+    // tuning knob for the in-tile ranking (see rs_ctx.hpp)
+    if (const char* r = std::getenv("RS_RANK")) c->rank_mode = std::strcmp(r, "match") == 0;
     DeviceGuard dg(device);
     if (!dg.ok || cudaMalloc(&c->d_area, 256) != cudaSuccess) {
         delete c;

@@ -13,13 +13,15 @@
 
 namespace rs {
 
-enum KernelClass : int { KC_HIST = 0, KC_PASS = 1, KC_FILL = 2, KC_COUNT_ };
+enum KernelClass : int { KC_HIST = 0, KC_PASS = 1, KC_FILL = 2, KC_PACK = 3, KC_SEG = 4, KC_COUNT_ };
 
 inline int kernel_class_of(const char* name) {
     if (!name) return -1;
     if (!std::strcmp(name, "hist")) return KC_HIST;
     if (!std::strcmp(name, "pass")) return KC_PASS;
     if (!std::strcmp(name, "fill")) return KC_FILL;
+    if (!std::strcmp(name, "pack")) return KC_PACK;
+    if (!std::strcmp(name, "seg")) return KC_SEG;
     return -1;
 }
 
@@ -43,6 +45,7 @@ struct rs_ctx {
     uint32_t last_passes_total = 0;
     uint32_t last_tiles = 0;
     bool timing = false;
+    int rank_mode = 0;  // 0: ballot ranking, 1: match-unit ranking (RS_RANK=match)
     std::vector<rs::TimedLaunch> timed[rs::KC_COUNT_];
     std::vector<cudaEvent_t> event_pool;
     std::mutex mu;

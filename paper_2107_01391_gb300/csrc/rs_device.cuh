@@ -133,21 +133,42 @@ __device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
     asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Lanes of the warp holding the same 8-bit digit: one ballot per bit.
+// Lanes of the warp holding the same 8-bit digit: one ballot per bit.  Per
+// bit: sx = all ones if the bit is set (bfe.s32 sign-extends the 1-bit field),
+// bal = lanes with the bit set, and peers &= ~(bal ^ sx) in one lop3
+// (truth table 0x90 for a & ~(b ^ c) with a = 0xF0, b = 0xCC, c = 0xAA).
 __device__ __forceinline__ uint32_t match_digit(uint32_t d) {
     uint32_t m = 0xffffffffu;
 #pragma unroll
     for (int b = 0; b < RADIX_BITS; b++) {
-        const uint32_t bit = (d >> b) & 1u;
-        const uint32_t bal = __ballot_sync(0xffffffffu, bit);
-        m &= bit ? bal : ~bal;
+        asm("{\n\t"
+            ".reg .pred p;\n\t"
+            ".reg .b32 sx, bal;\n\t"
+            "bfe.s32 sx, %1, %2, 1;\n\t"
+            "setp.ne.s32 p, sx, 0;\n\t"
+            "vote.sync.ballot.b32 bal, p, 0xffffffff;\n\t"
+            "lop3.b32 %0, %0, bal, sx, 0x90;\n\t"
+            "}"
+            : "+r"(m)
+            : "r"(d), "r"(b));
     }
     return m;
 }
 
 template <typename T>
 __device__ __forceinline__ uint32_t digit_of(T cell, uint32_t shift) {
-    return (uint32_t)(cell >> shift) & (RADIX - 1);
+    if constexpr (sizeof(T) == 4) {
+        // an 8-bit group is a whole byte: one byte permute extracts it
+        return __byte_perm((uint32_t)cell, 0u, 0x4440u | (shift >> 3));
+    } else {
+        return (uint32_t)(cell >> shift) & (RADIX - 1);
+    }
+}
+
+__device__ __forceinline__ uint32_t lanemask_gt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_gt;" : "=r"(m));
+    return m;
 }
 
 // Exclusive scan of one value per thread over a 256-thread block.

@@ -36,6 +36,7 @@ struct CountArgs {
     uint32_t* fill_offsets;  // [FILL_CELLS + 1]
     uint32_t* status;
     DevInfo* info;
+    const uint32_t* skip;  // nullable: a non-zero word makes the whole sort a no-op
 };
 
 // ----------------------------------------------------------------------------
@@ -45,10 +46,13 @@ template <class C>
 __device__ __forceinline__ void count_one(typename C::In key, const CountArgs& a,
                                           uint32_t (*sh)[RADIX], uint32_t* sfill, bool& ok,
                                           bool& big) {
-    const typename C::Cell cell = C::decode(key, a.prm, ok);
-    for (uint32_t p = 0; p < a.passes; p++) atomicAdd(&sh[p][digit_of(cell, p * RADIX_BITS)], 1u);
+    using Cell = typename C::Cell;
+    const Cell cell = C::decode(key, a.prm, ok);
+#pragma unroll
+    for (uint32_t p = 0; p < sizeof(Cell); p++)  // one 8-bit group per cell byte
+        if (p < a.passes) atomicAdd(&sh[p][digit_of(cell, p * RADIX_BITS)], 1u);
     if (a.fill_allowed && !big) {
-        if (cell < (typename C::Cell)FILL_CELLS)
+        if (cell < (Cell)FILL_CELLS)
             atomicAdd(&sfill[(uint32_t)cell], 1u);
         else
             big = true;
@@ -136,6 +140,7 @@ static __device__ void make_plan(const CountArgs& a, uint32_t* s_warp) {
 template <class C>
 __global__ void __launch_bounds__(BLOCK) count_kernel(CountArgs a) {
     using In = typename C::In;
+    if (a.skip && *a.skip) return;  // the plan stays zeroed: every pass inactive
     __shared__ uint32_t sh[MAX_PASSES][RADIX];
     __shared__ uint32_t sfill[FILL_CELLS];
     __shared__ uint32_t s_warp[WARPS];
@@ -239,7 +244,61 @@ __device__ __forceinline__ void* pick_dst(const PassArgs& a, uint32_t b, bool va
     return vals ? a.vals_out : a.keys_out;
 }
 
-template <class C, typename V, int IPT>
+// Peers of this lane's digit in the warp: RANK_BALLOT builds the mask from one
+// ballot per digit bit, RANK_MATCH asks the hardware match unit.
+enum : int { RANK_BALLOT = 0, RANK_MATCH = 1 };
+
+template <int RANK>
+__device__ __forceinline__ uint32_t peers_of(uint32_t d) {
+    if constexpr (RANK == RANK_MATCH)
+        return __match_any_sync(0xffffffffu, d);
+    else
+        return match_digit(d);
+}
+
+// Decoupled look-back for one cell: the sum of this cell's counts over all
+// tiles before `tile`, walking back four predecessors per round trip until a
+// tile that already holds its inclusive prefix.  The wait for an unpublished
+// predecessor is bounded; on expiry the status word records a timeout and the
+// partial sum is returned so that every tile still finishes.
+__device__ __forceinline__ uint32_t lookback_prefix(const uint32_t* lookback, uint32_t tile,
+                                                    uint32_t cell, uint32_t* status) {
+    uint32_t before = 0;
+    int64_t j = (int64_t)tile - 1;
+    const uint64_t t0 = global_ns();
+    uint32_t spins = 0;
+    while (j >= 0) {
+        uint32_t s[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+            s[q] = j - q >= 0 ? ld_relaxed(&lookback[(uint64_t)(j - q) * RADIX + cell])
+                              : LB_INCLUSIVE;
+        int consumed = 0;
+        bool done = false, blocked = false;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            if (done || blocked) continue;
+            const uint32_t flag = s[q] & ~LB_VALUE;
+            if (flag == 0) {
+                blocked = true;
+                continue;
+            }
+            before += s[q] & LB_VALUE;
+            consumed = q + 1;
+            done = flag == LB_INCLUSIVE;
+        }
+        if (done) break;
+        j -= consumed;
+        if (consumed == 0 && (++spins & 15u) == 0 &&
+            (global_ns() - t0 > LOOKBACK_TIMEOUT_NS || spins > LOOKBACK_MAX_POLLS)) {
+            atomicOr(status, STATUS_TIMEOUT);
+            break;  // give up; publish what we have so successors finish
+        }
+    }
+    return before;
+}
+
+template <class C, typename V, int IPT, int RANK>
 __global__ void __launch_bounds__(BLOCK) pass_kernel(PassArgs a) {
     using Cell = typename C::Cell;
     using In = typename C::In;
@@ -248,8 +307,9 @@ __global__ void __launch_bounds__(BLOCK) pass_kernel(PassArgs a) {
     constexpr int TILE = BLOCK * IPT;
     using VS = typename std::conditional<kPairs, V, uint32_t>::type;  // storage type
 
-    __shared__ uint32_t wh[WARPS][RADIX];     // per-warp digit counters, then prefixes
-    __shared__ uint32_t s_bin_excl[RADIX];    // tile-local start of each cell
+    // wh[w][d]: first the count of cell d in warp w's slice, then the
+    // tile-local position where warp w's next key of cell d goes
+    __shared__ uint32_t wh[WARPS][RADIX];
     __shared__ uint32_t s_bin_global[RADIX];  // global position of tile-local index 0 per cell
     __shared__ uint32_t s_warp[WARPS];
     __shared__ uint32_t s_tile;
@@ -273,58 +333,52 @@ __global__ void __launch_bounds__(BLOCK) pass_kernel(PassArgs a) {
     __syncthreads();
     const uint32_t tile = s_tile;
     const uint64_t tile_base = (uint64_t)tile * TILE;
-    const uint32_t valid = (uint32_t)min((uint64_t)TILE, a.n - tile_base);
+    const bool full = tile_base + TILE <= a.n;
+    const uint32_t valid = full ? TILE : (uint32_t)(a.n - tile_base);
 
     // ---- load (warp-striped: warp w owns inputs [w*32*IPT, (w+1)*32*IPT)) ----
     const uint64_t wbase = tile_base + (uint64_t)warp * 32 * IPT + lane;
     Cell k[IPT];
     VS v[IPT];
-    const void* ksrc = pick_src(a, P->src[a.pass], false);
+    const uint32_t src = P->src[a.pass];
     if (first) {
-        const In* in = static_cast<const In*>(ksrc);
+        const In* in = static_cast<const In*>(pick_src(a, src, false)) + wbase;
         bool ok = true;
+        if (full) {
 #pragma unroll
-        for (int i = 0; i < IPT; i++) {
-            const uint64_t idx = wbase + (uint64_t)i * 32;
-            k[i] = idx < a.n ? C::decode(__ldcs(&in[idx]), a.prm, ok) : ~Cell(0);
+            for (int i = 0; i < IPT; i++) k[i] = C::decode(__ldcs(&in[i * 32]), a.prm, ok);
+        } else {
+#pragma unroll
+            for (int i = 0; i < IPT; i++)
+                k[i] = wbase + i * 32 < a.n ? C::decode(__ldcs(&in[i * 32]), a.prm, ok) : ~Cell(0);
         }
     } else {
-        const Cell* in = static_cast<const Cell*>(ksrc);
+        const Cell* in = static_cast<const Cell*>(pick_src(a, src, false)) + wbase;
+        if (full) {
 #pragma unroll
-        for (int i = 0; i < IPT; i++) {
-            const uint64_t idx = wbase + (uint64_t)i * 32;
-            k[i] = idx < a.n ? __ldcs(&in[idx]) : ~Cell(0);
+            for (int i = 0; i < IPT; i++) k[i] = __ldcs(&in[i * 32]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < IPT; i++) k[i] = wbase + i * 32 < a.n ? __ldcs(&in[i * 32]) : ~Cell(0);
         }
     }
     if constexpr (kPairs) {
-        const VS* vin = static_cast<const VS*>(pick_src(a, P->src[a.pass], true));
+        const VS* vin = static_cast<const VS*>(pick_src(a, src, true)) + wbase;
+        if (full) {
 #pragma unroll
-        for (int i = 0; i < IPT; i++) {
-            const uint64_t idx = wbase + (uint64_t)i * 32;
-            v[i] = idx < a.n ? __ldcs(&vin[idx]) : VS(0);
+            for (int i = 0; i < IPT; i++) v[i] = __ldcs(&vin[i * 32]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < IPT; i++) v[i] = wbase + i * 32 < a.n ? __ldcs(&vin[i * 32]) : VS(0);
         }
     }
 
-    // ---- stable rank within the warp: items in input order (i, then lane) ----
-    uint32_t rank[IPT];
-    const uint32_t lt = lanemask_lt();
+    // ---- counts per (warp, cell): order does not matter here ----
 #pragma unroll
-    for (int i = 0; i < IPT; i++) {
-        const uint32_t d = digit_of(k[i], a.shift);
-        const uint32_t peers = match_digit(d);
-        const uint32_t leader = 31 - __clz(peers);
-        uint32_t old = 0;
-        if (lane == leader) {
-            old = wh[warp][d];
-            wh[warp][d] = old + __popc(peers);
-        }
-        old = __shfl_sync(0xffffffffu, old, leader);
-        rank[i] = old + __popc(peers & lt);
-        __syncwarp();
-    }
+    for (int i = 0; i < IPT; i++) atomicAdd(&wh[warp][digit_of(k[i], a.shift)], 1u);
     __syncthreads();
 
-    // ---- per-cell tile counts, warp prefixes, publish, tile-local offsets ----
+    // ---- tile count per cell, publish it, then tile-local starts ----
     uint32_t run = 0;
 #pragma unroll
     for (int w = 0; w < WARPS; w++) {
@@ -338,40 +392,33 @@ __global__ void __launch_bounds__(BLOCK) pass_kernel(PassArgs a) {
     st_relaxed(&lb[t], (tile == 0 ? LB_INCLUSIVE : LB_AGGREGATE) | count);
     uint32_t tile_total;
     const uint32_t excl = block_exclusive_scan(count, s_warp, &tile_total);
-    s_bin_excl[t] = excl;
+#pragma unroll
+    for (int w = 0; w < WARPS; w++) wh[w][t] += excl;
     __syncthreads();
 
-    // ---- scatter into shared memory in (cell, input) order ----
+    // ---- stable rank in (cell, input) order, scattered into shared memory ----
+    const uint32_t lt = lanemask_lt(), gt = lanemask_gt();
 #pragma unroll
     for (int i = 0; i < IPT; i++) {
         const uint32_t d = digit_of(k[i], a.shift);
-        const uint32_t pos = s_bin_excl[d] + wh[warp][d] + rank[i];
+        const uint32_t peers = peers_of<RANK>(d);
+        // every lane reads its cell's running position; the highest peer
+        // (the last of them in input order) advances it past the group
+        uint32_t* slot = &wh[warp][d];
+        const uint32_t at = *slot;
+        const uint32_t below = __popc(peers & lt);
+        __syncwarp();  // every peer has read the slot before it moves
+        if ((peers & gt) == 0) *slot = at + below + 1;
+        const uint32_t pos = at + below;
         s_keys[pos] = k[i];
         if constexpr (kPairs) s_vals[pos] = v[i];
+        __syncwarp();
     }
 
     // ---- decoupled look-back: this cell's count in all earlier tiles ----
     uint32_t before = 0;
     if (tile > 0) {
-        int64_t j = (int64_t)tile - 1;
-        const uint64_t t0 = global_ns();
-        uint32_t spins = 0;
-        while (true) {
-            const uint32_t s = ld_relaxed(&a.lookback[(uint64_t)j * RADIX + t]);
-            const uint32_t flag = s & ~LB_VALUE;
-            if (flag == 0) {
-                // bounded wait: by time, and by polls in case the timer stalls
-                if ((++spins & 63u) == 0 &&
-                    (global_ns() - t0 > LOOKBACK_TIMEOUT_NS || spins > LOOKBACK_MAX_POLLS)) {
-                    atomicOr(a.status, STATUS_TIMEOUT);
-                    break;  // give up; publish what we have so successors finish
-                }
-                continue;
-            }
-            before += s & LB_VALUE;
-            if (flag == LB_INCLUSIVE || j == 0) break;
-            --j;
-        }
+        before = lookback_prefix(a.lookback, tile, t, a.status);
         st_relaxed(&lb[t], LB_INCLUSIVE | ((before + count) & LB_VALUE));
     }
     s_bin_global[t] = a.bin_offsets[t] + before - excl;
@@ -382,19 +429,20 @@ __global__ void __launch_bounds__(BLOCK) pass_kernel(PassArgs a) {
     VS* vdst = kPairs ? static_cast<VS*>(pick_dst(a, P->dst[a.pass], true)) : nullptr;
     if (last) {
         Out* out = static_cast<Out*>(kdst);
+#pragma unroll 4
         for (uint32_t j = t; j < valid; j += BLOCK) {
             const Cell c = s_keys[j];
-            const uint32_t g = s_bin_global[digit_of(c, a.shift)] + j;
-            if (g >= a.n) continue;  // only after a timed-out wait
+            // the clamp only acts after a timed-out wait (output unspecified)
+            const uint32_t g = min(s_bin_global[digit_of(c, a.shift)] + j, (uint32_t)a.n - 1u);
             __stcs(&out[g], C::encode(c, a.prm));
             if constexpr (kPairs) __stcs(&vdst[g], s_vals[j]);
         }
     } else {
         Cell* out = static_cast<Cell*>(kdst);
+#pragma unroll 4
         for (uint32_t j = t; j < valid; j += BLOCK) {
             const Cell c = s_keys[j];
-            const uint32_t g = s_bin_global[digit_of(c, a.shift)] + j;
-            if (g >= a.n) continue;  // only after a timed-out wait
+            const uint32_t g = min(s_bin_global[digit_of(c, a.shift)] + j, (uint32_t)a.n - 1u);
             out[g] = c;
             if constexpr (kPairs) vdst[g] = s_vals[j];
         }

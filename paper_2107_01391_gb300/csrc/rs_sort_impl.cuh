@@ -65,10 +65,12 @@ inline int sm_count(int device) {
 }
 
 // One sort: keys_in (C::In) -> keys_out (C::Out), values V (NoVal = keys only).
+// skip (device pointer, may be NULL): when it holds a non-zero word at run
+// time the whole sort is a no-op (used by callers that plan on the device).
 template <class C, typename V>
 rs_status run_sort(rs_ctx* ctx, const void* keys_in, void* keys_out, const void* vals_in,
                    void* vals_out, size_t n, CodecParams prm, uint32_t cell_bits, void* temp,
-                   size_t* temp_bytes, cudaStream_t stream) {
+                   size_t* temp_bytes, cudaStream_t stream, const uint32_t* skip) {
     using Cell = typename C::Cell;
     constexpr bool kPairs = ValTraits<V>::kPairs;
     constexpr int IPT = ipt_for<C>();
@@ -115,6 +117,7 @@ rs_status run_sort(rs_ctx* ctx, const void* keys_in, void* keys_out, const void*
         a.fill_offsets = fill_offsets;
         a.status = ctx->d_status;
         a.info = static_cast<DevInfo*>(ctx->d_info);
+        a.skip = skip;
         LaunchTimer lt(ctx, KC_HIST, stream);
         count_kernel<C><<<count_grid(n, sm_count(ctx->device)), BLOCK, 0, stream>>>(a);
     }
@@ -131,12 +134,16 @@ rs_status run_sort(rs_ctx* ctx, const void* keys_in, void* keys_out, const void*
         fill_kernel<C><<<grid, BLOCK, 0, stream>>>(f);
     }
     using Smem = PassSmem<Cell, V, IPT>;
-    auto kern = pass_kernel<C, V, IPT>;
+    auto kern_ballot = pass_kernel<C, V, IPT, RANK_BALLOT>;
+    auto kern_match = pass_kernel<C, V, IPT, RANK_MATCH>;
+    auto kern = ctx->rank_mode == RANK_MATCH ? kern_match : kern_ballot;
     // static + dynamic shared memory may exceed the 48 KB default: opt in
     // once per device for this instantiation
     static bool smem_set[64] = {};
     if (ctx->device < 64 && !smem_set[ctx->device]) {
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (cudaFuncSetAttribute(kern_ballot, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)Smem::kBytes) != cudaSuccess ||
+            cudaFuncSetAttribute(kern_match, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)Smem::kBytes) != cudaSuccess)
             return RS_ERR_CUDA;
         smem_set[ctx->device] = true;
@@ -169,6 +176,7 @@ rs_status run_sort(rs_ctx* ctx, const void* keys_in, void* keys_out, const void*
 
 #define RS_DECLARE_SORT(C, V)                                                                  \
     template rs_status run_sort<C, V>(rs_ctx*, const void*, void*, const void*, void*, size_t, \
-                                      CodecParams, uint32_t, void*, size_t*, cudaStream_t);
+                                      CodecParams, uint32_t, void*, size_t*, cudaStream_t,      \
+                                      const uint32_t*);
 
 }  // namespace rs

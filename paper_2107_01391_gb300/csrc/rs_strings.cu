@@ -1,0 +1,210 @@
+// rs_strings.cu -- rs_sort_strings: stable sort of byte strings.
+//
+// The paper claims strings (Table 2, "PS: Yes") without giving an algorithm.
+// Reading: one dimension of the count space per character position (Eq. 1,
+// Eq. 2), with a padding symbol below every byte for positions past a
+// string's end (the §3.1.2 pre-condition of equal digit counts).  The order
+// is unsigned-byte lexicographic with a proper prefix first.
+//
+// GPU form:
+//   1. alphabet_kernel: which byte values occur, and the longest string.  The
+//      radix of every position is then (distinct bytes + 1): symbol 0 is the
+//      pad, byte b maps to 1 + (number of present bytes below b), so symbol
+//      order is byte order.  w = bits per symbol (5 for 'a'..'z').
+//   2. The positions are grouped into chunks of s = floor(64 / w) symbols,
+//      each packed most significant first into a 64-bit cell: a chunk's cell
+//      is the row-major index of the chunk's sub-hypercube.
+//   3. Chunks are sorted least significant first (the later positions are
+//      sorted first, as buckets of the earlier ones, §2.2) as (cell, string
+//      index) pairs with the ordinary digit-group passes; every chunk after
+//      the first gathers its cells through the permutation so far.
+// Chunks wholly past the longest string are skipped on the device.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "../../include/rs.h"
+#include "rs_sort_impl.cuh"
+
+namespace rs {
+
+
+namespace {
+
+constexpr uint32_t kMinSymbolsPerChunk = 7;  // 64 / 9 bits (256 bytes + pad)
+
+// Device-side description of the key space, written by alphabet_plan.
+struct StrPlan {
+    uint32_t present[RADIX];  // byte value occurs (0/1), then its symbol
+    uint32_t longest;         // longest string seen (clamped to max_len)
+    uint32_t width;           // bits per symbol
+    uint32_t per_chunk;       // symbols per 64-bit cell
+    uint32_t chunks;          // chunks that hold any symbol
+    uint32_t done;            // CTAs of alphabet_kernel finished
+    uint32_t skip[1];         // per-chunk skip flags follow (chunks_max entries)
+};
+
+__global__ void __launch_bounds__(BLOCK) alphabet_kernel(const uint8_t* chars,
+                                                         const uint32_t* offsets, uint64_t n,
+                                                         uint32_t max_len, uint32_t chunks_max,
+                                                         StrPlan* sp, uint32_t* status) {
+    __shared__ uint32_t s_present[RADIX];
+    __shared__ uint32_t s_longest;
+    __shared__ uint32_t s_last;
+    const uint32_t t = threadIdx.x;
+    s_present[t] = 0;
+    if (t == 0) s_longest = 0;
+    __syncthreads();
+    const uint64_t gtid = (uint64_t)blockIdx.x * BLOCK + t;
+    const uint64_t gsize = (uint64_t)gridDim.x * BLOCK;
+    bool bad = false;
+    uint32_t longest = 0;
+    for (uint64_t i = gtid; i < n; i += gsize) {
+        const uint32_t b = offsets[i], e = offsets[i + 1];
+        if (e < b || e > offsets[n]) {
+            bad = true;  // offsets must not decrease nor pass offsets[n]
+            continue;
+        }
+        uint32_t len = e - b;
+        if (len > max_len) {
+            bad = true;
+            len = max_len;
+        }
+        longest = max(longest, len);
+    }
+    // bytes that occur: the char buffer between the first and last offset
+    const uint32_t c0 = n ? offsets[0] : 0, c1 = n ? offsets[n] : 0;
+    for (uint64_t c = (uint64_t)c0 + gtid; c < c1; c += gsize) {
+        const uint32_t b = chars[c];
+        if (!s_present[b]) s_present[b] = 1;  // benign race: every writer stores 1
+    }
+    if (bad) atomicOr(status, STATUS_RANGE);
+    atomicMax(&s_longest, longest);
+    __syncthreads();
+    if (s_present[t]) sp->present[t] = 1;
+    if (t == 0) atomicMax(&sp->longest, s_longest);
+    __threadfence();
+    __syncthreads();
+    if (t == 0) s_last = atomicAdd(&sp->done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // last CTA: symbols (exclusive count of present bytes below b, plus one)
+    __shared__ uint32_t s_warp[WARPS];
+    const uint32_t p = __ldcg(&sp->present[t]);
+    uint32_t distinct;
+    const uint32_t below = block_exclusive_scan(p, s_warp, &distinct);
+    sp->present[t] = p ? below + 1 : 0;
+    if (t == 0) {
+        uint32_t w = 1;
+        while ((1u << w) <= distinct) w++;  // symbols 0..distinct need w bits
+        const uint32_t s = 64 / w;
+        const uint32_t longest_all = __ldcg(&sp->longest);
+        // at least one chunk, so that all-empty input still yields the identity
+        const uint32_t chunks = longest_all ? (longest_all + s - 1) / s : 1;
+        sp->width = w;
+        sp->per_chunk = s;
+        sp->chunks = chunks;
+        for (uint32_t c = 0; c < chunks_max; c++) sp->skip[c] = c >= chunks;
+    }
+}
+
+// Cells of chunk c: symbols [c*s, (c+1)*s) of each string, packed most
+// significant first.  The first chunk processed reads strings in input order;
+// later chunks read string perm[j] for output slot j.
+__global__ void __launch_bounds__(BLOCK) pack_kernel(const uint8_t* chars, const uint32_t* offsets,
+                                                     uint64_t n, uint32_t max_len, uint32_t c,
+                                                     const StrPlan* sp, uint64_t* cells,
+                                                     uint32_t* idx) {
+    if (sp->skip[c]) return;
+    const uint64_t j = (uint64_t)blockIdx.x * BLOCK + threadIdx.x;
+    if (j >= n) return;
+    const bool first = c + 1 == sp->chunks;
+    const uint32_t i = first ? (uint32_t)j : idx[j];
+    // stay inside chars[0, offsets[n]) even for malformed offsets (flagged
+    // as RS_ERR_RANGE by alphabet_kernel)
+    const uint32_t end = offsets[n];
+    const uint32_t b = min(offsets[i], end), e = min(offsets[i + 1], end);
+    const uint32_t len = e < b ? 0u : min(e - b, max_len);
+    const uint32_t w = sp->width, s = sp->per_chunk;
+    const uint32_t p0 = c * s;
+    uint64_t cell = 0;
+    for (uint32_t q = 0; q < s; q++) {
+        const uint32_t pos = p0 + q;
+        const uint32_t sym = pos < len ? sp->present[chars[b + pos]] : 0u;
+        cell = (cell << w) | sym;
+    }
+    cells[j] = cell;
+    idx[j] = i;
+}
+
+}  // namespace
+}  // namespace rs
+
+using namespace rs;
+
+extern "C" rs_status rs_sort_strings(rs_ctx* ctx, const uint8_t* chars, const uint32_t* offsets,
+                                     size_t n, uint32_t max_len, uint32_t* perm_out, void* temp,
+                                     size_t* temp_bytes, rs_stream_t stream) {
+    if (!ctx || !temp_bytes) return RS_ERR_INVALID;
+    if (n > RS_MAX_N || max_len == 0 || max_len > RS_MAX_STRING_LEN) return RS_ERR_INVALID;
+    if (n > 0 && (!offsets || !perm_out || (reinterpret_cast<uintptr_t>(offsets) % 4) ||
+                  (reinterpret_cast<uintptr_t>(perm_out) % 4)))
+        return RS_ERR_INVALID;
+    const uint32_t chunks_max = (max_len + kMinSymbolsPerChunk - 1) / kMinSymbolsPerChunk;
+    cudaStream_t st = (cudaStream_t)stream;
+
+    // workspace: [StrPlan + skip flags][cells u64 n][idx u32 n][pairs-sort workspace]
+    size_t sort_bytes = 0;
+    rs_status s = run_sort<CodecU64, uint32_t>(ctx, nullptr, nullptr, nullptr, nullptr, n,
+                                                    CodecParams{0}, 64, nullptr, &sort_bytes, st,
+                                                    nullptr);
+    if (s != RS_OK) return s;
+    const size_t plan_bytes = align_up(sizeof(StrPlan) + sizeof(uint32_t) * chunks_max);
+    const size_t cells_off = plan_bytes;
+    const size_t idx_off = cells_off + align_up(sizeof(uint64_t) * std::max<size_t>(n, 1));
+    const size_t sort_off = idx_off + align_up(sizeof(uint32_t) * std::max<size_t>(n, 1));
+    const size_t total = sort_off + sort_bytes;
+    if (!temp) {
+        *temp_bytes = total;
+        return RS_OK;
+    }
+    if (*temp_bytes < total) return RS_ERR_TEMP_TOO_SMALL;
+    if (reinterpret_cast<uintptr_t>(temp) % 256) return RS_ERR_INVALID;
+    if (n == 0) return RS_OK;
+    if (!chars) return RS_ERR_INVALID;
+
+    DeviceGuard dg(ctx->device);
+    if (!dg.ok) return RS_ERR_CUDA;
+    unsigned char* T = static_cast<unsigned char*>(temp);
+    StrPlan* sp = reinterpret_cast<StrPlan*>(T);
+    uint64_t* cells = reinterpret_cast<uint64_t*>(T + cells_off);
+    uint32_t* idx = reinterpret_cast<uint32_t*>(T + idx_off);
+    void* sort_temp = T + sort_off;
+
+    if (cudaMemsetAsync(T, 0, plan_bytes, st) != cudaSuccess) return RS_ERR_CUDA;
+    {
+        const int grid = (int)std::min<size_t>((n + BLOCK * 8 - 1) / (BLOCK * 8),
+                                               (size_t)sm_count(ctx->device) * 4);
+        LaunchTimer lt(ctx, KC_PACK, st);
+        alphabet_kernel<<<std::max(grid, 1), BLOCK, 0, st>>>(chars, offsets, n, max_len,
+                                                            chunks_max, sp, ctx->d_status);
+    }
+    const unsigned grid_n = (unsigned)((n + BLOCK - 1) / BLOCK);
+    for (int c = (int)chunks_max - 1; c >= 0; c--) {
+        {
+            LaunchTimer lt(ctx, KC_PACK, st);
+            pack_kernel<<<grid_n, BLOCK, 0, st>>>(chars, offsets, n, max_len, (uint32_t)c, sp,
+                                                  cells, idx);
+        }
+        size_t tb = sort_bytes;
+        s = run_sort<CodecU64, uint32_t>(ctx, cells, cells, idx, idx, n, CodecParams{0}, 64,
+                                              sort_temp, &tb, st, &sp->skip[c]);
+        if (s != RS_OK) return s;
+    }
+    if (cudaMemcpyAsync(perm_out, idx, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st) !=
+        cudaSuccess)
+        return RS_ERR_CUDA;
+    return cudaGetLastError() == cudaSuccess ? RS_OK : RS_ERR_CUDA;
+}
