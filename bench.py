@@ -51,6 +51,7 @@ def parse():
     # smaller arrays for ncu captures only; a line printed with --log2n != 28
     # is not a benchmark result
     ap.add_argument("--log2n", type=int, default=28)
+    ap.add_argument("--no-segmented", action="store_true")
     return ap.parse_args()
 
 
@@ -168,6 +169,83 @@ def cpu_baseline(sample_n: int):
     return {"value": sample_n / dt, "unit": "keys/s", "cores": 1, "kind": "oracle",
             "sample": f"first {sample_n} keys (2^{int(np.log2(sample_n))}) of the uniform "
                       f"u32-pairs workload, one oracle call, {dt:.2f} s single-threaded"}
+
+
+def segmented_leg(binding, ctx, steps: int, warmup: int):
+    """Batched segmented sort against one call per segment, same GPU, same data.
+
+    Workload: 65536 segments with log-uniform sizes in [16, 2^20], rescaled so
+    they sum to 2^28 keys (u32 keys, f32 values).  Both forms go through the
+    C ABI; the per-call form issues one rs_sort_pairs per segment on the same
+    stream with preallocated outputs and workspace.
+    """
+    import ctypes
+    import torch
+    from paper_2107_01391_gb300 import workloads as W
+    sizes = W.segment_sizes(65536, total=1 << 28)
+    keys, vals, off = W.segments(sizes)
+    n = keys.size
+    dk = torch.from_numpy(keys.view(np.int32)).cuda()
+    dv = torch.from_numpy(vals).cuda()
+    doff = torch.from_numpy(off.view(np.int64)).cuda()
+    ko, vo = torch.empty_like(dk), torch.empty_like(dv)
+    stream = torch.cuda.current_stream()
+    temp = None
+    for _ in range(warmup):
+        _, _ = binding.rs_sort_segmented(dk, doff, dv, ko, vo, ctx=ctx, temp=temp)
+    ctx.check()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = ctx.launch_count()
+    e0.record(stream)
+    for _ in range(steps):
+        binding.rs_sort_segmented(dk, doff, dv, ko, vo, ctx=ctx)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ctx.check()
+    batched_ms = e0.elapsed_time(e1) / steps
+    seg_launches = (ctx.launch_count() - launches0) / steps
+
+    # one call per segment: raw C-ABI calls in a loop
+    L = binding.lib()
+    big = int(sizes.max())
+    need = ctypes.c_size_t(0)
+    z = ctypes.c_void_p(256)
+    L.rs_sort_pairs(ctx.handle, binding.RS_KEY_U32, z, z, z, z, 4, big, None, None,
+                    ctypes.byref(need), None)
+    tmp = torch.empty(need.value, dtype=torch.uint8, device="cuda")
+    kb, vb, ob, pb = dk.data_ptr(), dv.data_ptr(), ko.data_ptr(), vo.data_ptr()
+    sptr = ctypes.c_void_p(stream.cuda_stream)
+    tptr = ctypes.c_void_p(tmp.data_ptr())
+    starts = off[:-1].astype(np.int64).tolist()
+    lens = sizes.astype(np.int64).tolist()
+
+    def per_call():
+        for lo, ln in zip(starts, lens):
+            tb = ctypes.c_size_t(need.value)
+            rc = L.rs_sort_pairs(ctx.handle, 0, ctypes.c_void_p(kb + 4 * lo),
+                                 ctypes.c_void_p(ob + 4 * lo), ctypes.c_void_p(vb + 4 * lo),
+                                 ctypes.c_void_p(pb + 4 * lo), 4, ln, None, tptr,
+                                 ctypes.byref(tb), sptr)
+            if rc:
+                raise RuntimeError(f"rs_sort_pairs failed: {rc}")
+
+    per_call()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    per_call()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ctx.check()
+    per_call_ms = e0.elapsed_time(e1)
+    del dk, dv, ko, vo, tmp
+    torch.cuda.empty_cache()
+    return {"workload": "65536 segments, log-uniform sizes 16..2^20 rescaled to sum 2^28 "
+                        "(Run B), u32 keys + f32 values",
+            "total_keys": int(n), "num_segs": int(sizes.size), "max_seg": big,
+            "batched_ms": batched_ms, "batched_keys_per_s": n / (batched_ms * 1e-3),
+            "batched_launches": seg_launches,
+            "per_call_ms": per_call_ms, "per_call_keys_per_s": n / (per_call_ms * 1e-3),
+            "speedup": per_call_ms / batched_ms}
 
 
 def run_reference(args):
@@ -315,6 +393,10 @@ def run_ours(args):
                "ms_per_step": ms_e2e, "steps": steps}
         del dk, dv, ko, vo, temp
 
+    seg = None
+    if not args.no_segmented and world == 1:
+        seg = segmented_leg(binding, ctx, max(1, min(args.steps, 10)), max(1, min(args.warmup, 3)))
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -358,6 +440,7 @@ def run_ours(args):
                       "pass_ms_avg": r["pass_ms_avg"], "count_ms_avg": r["count_ms_avg"],
                       "passes_run": r["passes_run"]} for d, r in results.items()},
         "e2e": e2e,
+        "segmented": seg,
         "cpu_baseline": (cpu_baseline(ORACLE_SAMPLE)
                          if world == 1 and not args.no_cpu_baseline else None),
     }

@@ -62,7 +62,10 @@ typedef enum rs_status {
 typedef enum rs_key_type {
     RS_KEY_U32 = 0,     /* uint32_t */
     RS_KEY_U64 = 1,     /* uint64_t */
-    RS_KEY_I64_DEC = 2  /* int64_t fixed-point decimal, see rs_key_params */
+    RS_KEY_I64_DEC = 2, /* int64_t fixed-point decimal, see rs_key_params */
+    RS_KEY_F32 = 3,     /* float: -0.0 ties with +0.0 and is written as +0.0;
+                           NaNs sort last and are written as the quiet NaN */
+    RS_KEY_F64 = 4      /* double, same rules as RS_KEY_F32 */
 } rs_key_type;
 
 /* Digit layout of a fixed-point decimal key (RS_KEY_I64_DEC): the value
@@ -146,6 +149,30 @@ rs_status rs_sort_pairs(rs_ctx* ctx, rs_key_type kt, const void* keys_in, void* 
 rs_status rs_sort_strings(rs_ctx* ctx, const uint8_t* chars, const uint32_t* offsets, size_t n,
                           uint32_t max_len, uint32_t* perm_out, void* temp, size_t* temp_bytes,
                           rs_stream_t stream);
+
+/* Segmented sort: num_segs independent stable sorts in one call.  Segment
+ * s covers positions [seg_offsets[s], seg_offsets[s+1]) of the arrays; every
+ * segment is a bucket of its own (§2.2).  Positions outside every segment
+ * are left unwritten.
+ *   kt, params  key type as in rs_sort_pairs (RS_KEY_F32/F64 allowed here);
+ *   n           length of the key (and value) arrays;
+ *   seg_offsets device uint64_t[num_segs+1], non-decreasing, at most n; or
+ *               NULL for num_segs equal segments of n / num_segs keys (n
+ *               must be a multiple of num_segs);
+ *   vals_in/out NULL/NULL: keys only.  vals_in given: values move with
+ *               their keys.  vals_in NULL with vals_out given: vals_out
+ *               receives, for every output position, the index within its
+ *               segment of the key placed there (an argsort), as val_bytes
+ *               (4 or 8) unsigned integers.
+ * Offsets that decrease or pass n raise RS_ERR_RANGE (device-detected) and
+ * the offending segment is skipped.  One launch sorts every segment: segments
+ * of at most 4096 keys are sorted on chip in one read and one write; larger
+ * ones by one CTA each, largest first. */
+rs_status rs_sort_segmented(rs_ctx* ctx, rs_key_type kt, const void* keys_in, void* keys_out,
+                            const void* vals_in, void* vals_out, size_t val_bytes, size_t n,
+                            const uint64_t* seg_offsets, size_t num_segs,
+                            const rs_key_params* params, void* temp, size_t* temp_bytes,
+                            rs_stream_t stream);
 
 /* ------------------------------------------------------- no allocation */
 

@@ -25,7 +25,7 @@ RS_OK, RS_ERR_INVALID, RS_ERR_RANGE, RS_ERR_TEMP_TOO_SMALL = 0, 1, 2, 3
 RS_ERR_CUDA, RS_ERR_TIMEOUT, RS_ERR_UNSUPPORTED = 4, 5, 6
 STATUS_NAMES = {0: "RS_OK", 1: "RS_ERR_INVALID", 2: "RS_ERR_RANGE", 3: "RS_ERR_TEMP_TOO_SMALL",
                 4: "RS_ERR_CUDA", 5: "RS_ERR_TIMEOUT", 6: "RS_ERR_UNSUPPORTED"}
-RS_KEY_U32, RS_KEY_U64, RS_KEY_I64_DEC = 0, 1, 2
+RS_KEY_U32, RS_KEY_U64, RS_KEY_I64_DEC, RS_KEY_F32, RS_KEY_F64 = 0, 1, 2, 3, 4
 RS_MAX_N = (1 << 30) - 1
 RS_FILL_CELLS = 4096
 
@@ -336,6 +336,72 @@ def rs_sort_strings(chars: torch.Tensor, offsets: torch.Tensor, max_len: int,
     temp, tb = _workspace(call, offsets.device, temp)
     _check(call(_ptr(temp), ctypes.byref(tb)), "rs_sort_strings")
     return perm_out
+
+
+def _seg_key_type(keys: torch.Tensor, decimal):
+    if decimal is not None:
+        return RS_KEY_I64_DEC
+    return {torch.uint32: RS_KEY_U32, torch.int32: RS_KEY_U32, torch.uint64: RS_KEY_U64,
+            torch.int64: RS_KEY_U64, torch.float32: RS_KEY_F32,
+            torch.float64: RS_KEY_F64}[keys.dtype]
+
+
+def rs_sort_segmented(keys: torch.Tensor, seg_offsets: torch.Tensor | None,
+                      values: torch.Tensor | None = None, keys_out: torch.Tensor | None = None,
+                      values_out: torch.Tensor | None = None, *, num_segs: int | None = None,
+                      argsort: bool = False, index_dtype=torch.int64,
+                      decimal: tuple[int, int] | None = None, ctx: Context | None = None,
+                      stream=None, temp: torch.Tensor | None = None):
+    """Sort every segment of ``keys`` independently and stably.
+
+    ``seg_offsets`` (int64 CUDA tensor, num_segs+1 entries) delimits the
+    segments; ``None`` with ``num_segs`` means equal segments.  Returns
+    (sorted keys, sorted values) when ``values`` is given, (sorted keys,
+    indices within each segment) when ``argsort``, else the sorted keys.
+    Float keys: -0.0 ties with +0.0 and comes out as +0.0; NaNs sort last.
+    """
+    kt = _seg_key_type(keys, decimal)
+    _cuda(keys, "keys", keys.element_size(), (keys.dtype,))
+    n = keys.numel()
+    if seg_offsets is not None:
+        _cuda(seg_offsets, "seg_offsets", 8, (torch.int64, torch.uint64))
+        num_segs = seg_offsets.numel() - 1
+    elif num_segs is None:
+        raise ValueError("give seg_offsets or num_segs")
+    keys_out = torch.empty_like(keys) if keys_out is None else keys_out
+    if values is not None:
+        vb = values.element_size()
+        _cuda(values, "values", vb, (values.dtype,))
+        values_out = torch.empty_like(values) if values_out is None else values_out
+    elif argsort:
+        values_out = (torch.empty(keys.shape, dtype=index_dtype, device=keys.device)
+                      if values_out is None else values_out)
+        vb = values_out.element_size()
+    else:
+        vb = 0
+    ctx = ctx or default_context(keys.device.index)
+    L = lib()
+    fn = L.rs_sort_segmented
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_size_t,
+                   ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(KeyParams), ctypes.c_void_p,
+                   ctypes.POINTER(ctypes.c_size_t), ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    prm = KeyParams(*(decimal or (0, 0)))
+    s = _stream(keys, stream)
+    vin = _ptr(values) if values is not None else ctypes.c_void_p(0)
+    vout = _ptr(values_out) if values_out is not None else ctypes.c_void_p(0)
+    offs = _ptr(seg_offsets) if seg_offsets is not None else ctypes.c_void_p(0)
+
+    def call(t, b):
+        return fn(ctx.handle, kt, _ptr(keys), _ptr(keys_out), vin, vout, vb, n, offs, num_segs,
+                  ctypes.byref(prm), t, b, s)
+
+    temp, tb = _workspace(call, keys.device, temp)
+    _check(call(_ptr(temp), ctypes.byref(tb)), "rs_sort_segmented")
+    if values_out is not None:
+        return keys_out, values_out
+    return keys_out
 
 
 def rs_sort_u32_noalloc(keys: torch.Tensor, out: torch.Tensor | None = None,

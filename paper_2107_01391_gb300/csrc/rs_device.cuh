@@ -107,6 +107,41 @@ struct CodecDec {
     }
 };
 
+// IEEE floats as cells: flipping the sign bit of non-negative values and
+// every bit of negative ones makes unsigned order equal numeric order.  Before
+// that, -0.0 becomes +0.0 and every NaN the positive quiet NaN, so zeros tie
+// and NaNs sort last (the order torch.sort gives); the keys written out are
+// those canonical values.
+struct CodecF32 {
+    using In = uint32_t;  // the float's bits
+    using Cell = uint32_t;
+    using Out = uint32_t;
+    __device__ static Cell decode(In u, const CodecParams&, bool&) {
+        if (u == 0x80000000u) u = 0;                                  // -0.0
+        if ((u & 0x7f800000u) == 0x7f800000u && (u & 0x007fffffu)) u = 0x7fc00000u;  // NaN
+        return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+    }
+    __device__ static Out encode(Cell c, const CodecParams&) {
+        return (c & 0x80000000u) ? (c & 0x7fffffffu) : ~c;
+    }
+};
+
+struct CodecF64 {
+    using In = uint64_t;  // the double's bits
+    using Cell = uint64_t;
+    using Out = uint64_t;
+    __device__ static Cell decode(In u, const CodecParams&, bool&) {
+        constexpr uint64_t SIGN = 0x8000000000000000ull, EXP = 0x7ff0000000000000ull;
+        if (u == SIGN) u = 0;
+        if ((u & EXP) == EXP && (u & ~(SIGN | EXP))) u = 0x7ff8000000000000ull;
+        return (u & SIGN) ? ~u : (u | SIGN);
+    }
+    __device__ static Out encode(Cell c, const CodecParams&) {
+        constexpr uint64_t SIGN = 0x8000000000000000ull;
+        return (c & SIGN) ? (c & ~SIGN) : ~c;
+    }
+};
+
 // ------------------------------------------------------------------ helpers
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }

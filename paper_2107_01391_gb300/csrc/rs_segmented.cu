@@ -46,8 +46,10 @@ struct SegArgs {
     void* keys_tmp;
     void* vals_tmp;
     uint64_t n;
-    const uint64_t* seg_offsets;
+    const uint64_t* seg_offsets;  // NULL: equal segments of seg_len keys
+    uint64_t seg_len;
     uint64_t num_segs;
+    uint32_t iota;                // payload = index of the key within its segment
     const uint32_t* order;
     SegControl* ctl;
     uint32_t passes;
@@ -63,6 +65,11 @@ __device__ __forceinline__ uint32_t size_class(uint64_t len) {
 
 __device__ __forceinline__ bool seg_bounds(const SegArgs& a, uint64_t s, uint64_t& lo,
                                            uint64_t& hi) {
+    if (!a.seg_offsets) {
+        lo = s * a.seg_len;
+        hi = lo + a.seg_len;
+        return true;
+    }
     lo = a.seg_offsets[s];
     hi = a.seg_offsets[s + 1];
     return lo <= hi && hi <= a.n;
@@ -111,11 +118,13 @@ __global__ void __launch_bounds__(BLOCK) seg_order_kernel(SegArgs a, uint32_t* o
     }
 }
 
-// Load one tile (positions [base, base+valid) of `src`) warp-striped.
+// Load one tile (positions [base, base+valid) of `src`) warp-striped.  With
+// iota_from != ~0 the values are generated: position - iota_from.
 template <class C, typename VS, bool kPairs, bool kDecode>
 __device__ __forceinline__ void load_tile(const void* ksrc, const VS* vsrc, uint64_t base,
                                           uint32_t valid, const CodecParams& prm,
-                                          typename C::Cell (&k)[SEG_IPT], VS (&v)[SEG_IPT]) {
+                                          uint64_t iota_from, typename C::Cell (&k)[SEG_IPT],
+                                          VS (&v)[SEG_IPT], uint32_t* status) {
     using Cell = typename C::Cell;
     const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
     const uint32_t w0 = warp * 32 * SEG_IPT + lane;
@@ -128,9 +137,11 @@ __device__ __forceinline__ void load_tile(const void* ksrc, const VS* vsrc, uint
                 k[i] = C::decode(static_cast<const typename C::In*>(ksrc)[base + j], prm, ok);
             else
                 k[i] = static_cast<const Cell*>(ksrc)[base + j];
-            if constexpr (kPairs) v[i] = vsrc[base + j];
+            if constexpr (kPairs)
+                v[i] = iota_from != ~0ull ? (VS)(base + j - iota_from) : vsrc[base + j];
         }
     }
+    if (!ok) atomicOr(status, STATUS_RANGE);
 }
 
 template <class C, typename V>
@@ -171,7 +182,8 @@ __global__ void __launch_bounds__(BLOCK) seg_sort_kernel(SegArgs a) {
         if (len <= SEG_TILE) {
             // ---- one tile: sorted on chip, read once and written once ----
             const uint32_t valid = (uint32_t)len;
-            load_tile<C, VS, kPairs, true>(a.keys_in, vin, lo, valid, a.prm, k, v);
+            load_tile<C, VS, kPairs, true>(a.keys_in, vin, lo, valid, a.prm,
+                                           a.iota ? lo : ~0ull, k, v, a.status);
             for (uint32_t p = 0; p < a.passes; p++) {
                 rank_scatter<Cell, VS, SEG_IPT, kPairs>(k, v, valid, p * RADIX_BITS, ts,
                                                         s_keys, s_vals);
@@ -232,14 +244,16 @@ __global__ void __launch_bounds__(BLOCK) seg_sort_kernel(SegArgs a) {
         for (uint32_t p = 0; p < a.passes; p++) act += s_active[p];
         bool use[MAX_PASSES];
         for (uint32_t p = 0; p < MAX_PASSES; p++) use[p] = p < a.passes && s_active[p];
-        if (a.in_is_out ? (act & 1u) : (act == 0)) {
-            for (uint32_t p = 0; p < a.passes; p++)
-                if (!use[p]) {
-                    use[p] = true;
-                    act++;
-                    break;
-                }
-        }
+        // (the pass count is even, so a trivial group is always there to
+        // switch on; an argsort must run at least once to write its indices)
+        uint32_t need = a.in_is_out ? (act & 1u) : (act == 0);
+        if (a.in_is_out && act == 0 && a.iota) need = 2;
+        for (uint32_t p = 0; p < a.passes && need; p++)
+            if (!use[p]) {
+                use[p] = true;
+                act++;
+                need--;
+            }
         uint32_t done = 0;
         uint32_t src_buf = BUF_IN;
         for (uint32_t p = 0; p < a.passes; p++) {
@@ -247,26 +261,40 @@ __global__ void __launch_bounds__(BLOCK) seg_sort_kernel(SegArgs a) {
             const uint32_t from_end = act - 1 - done;
             const uint32_t dst_buf = (from_end & 1u) ? BUF_TMP : BUF_OUT;
             const bool first = done == 0, last = from_end == 0;
-            const void* ksrc = src_buf == BUF_IN ? a.keys_in
-                                                 : (src_buf == BUF_TMP ? a.keys_tmp : a.keys_out);
+            // Every buffer is addressed from this segment's own start.  Cells
+            // parked in OUT live inside the segment's byte range of OUT, which
+            // matters when a cell is narrower than an output key (decimal
+            // keys: 32-bit cells in an int64 buffer) -- indexing OUT as a cell
+            // array would run into the next segments' bytes.
+            auto cell_base = [&](uint32_t b) -> void* {
+                if (b == BUF_TMP) return static_cast<Cell*>(a.keys_tmp) + lo;
+                return static_cast<unsigned char*>(a.keys_out) + lo * sizeof(Out);
+            };
+            const void* ksrc = src_buf == BUF_IN
+                                   ? static_cast<const void*>(static_cast<const In*>(a.keys_in) + lo)
+                                   : cell_base(src_buf);
             const VS* vsrc = static_cast<const VS*>(
                 src_buf == BUF_IN ? a.vals_in : (src_buf == BUF_TMP ? a.vals_tmp : a.vals_out));
-            void* kdst = dst_buf == BUF_TMP ? a.keys_tmp : a.keys_out;
+            if (vsrc) vsrc += lo;
+            void* kdst = cell_base(dst_buf);
             VS* vdst = static_cast<VS*>(dst_buf == BUF_TMP ? a.vals_tmp : a.vals_out);
+            if (vdst) vdst += lo;
             const uint32_t shift = p * RADIX_BITS;
             s_run[t] = s_hist[p][t];
             __syncthreads();
-            for (uint64_t base = lo; base < hi; base += SEG_TILE) {
-                const uint32_t valid = (uint32_t)min((uint64_t)SEG_TILE, hi - base);
+            for (uint64_t base = 0; base < len; base += SEG_TILE) {
+                const uint32_t valid = (uint32_t)min((uint64_t)SEG_TILE, len - base);
                 if (first)
-                    load_tile<C, VS, kPairs, true>(ksrc, vsrc, base, valid, a.prm, k, v);
+                    load_tile<C, VS, kPairs, true>(ksrc, vsrc, base, valid, a.prm,
+                                                   a.iota ? 0ull : ~0ull, k, v, a.status);
                 else
-                    load_tile<C, VS, kPairs, false>(ksrc, vsrc, base, valid, a.prm, k, v);
+                    load_tile<C, VS, kPairs, false>(ksrc, vsrc, base, valid, a.prm, ~0ull, k, v,
+                                                    a.status);
                 rank_scatter<Cell, VS, SEG_IPT, kPairs>(k, v, valid, shift, ts, s_keys, s_vals);
                 for (uint32_t j = t; j < valid; j += BLOCK) {
                     const Cell c = s_keys[j];
                     const uint32_t d = digit_of(c, shift);
-                    const uint64_t g = lo + s_run[d] + (j - ts.excl[d]);
+                    const uint64_t g = s_run[d] + (j - ts.excl[d]);  // within the segment
                     if (last)
                         static_cast<Out*>(kdst)[g] = C::encode(c, a.prm);
                     else
@@ -294,7 +322,7 @@ template <class C, typename V>
 rs_status run_segmented(rs_ctx* ctx, const void* keys_in, void* keys_out, const void* vals_in,
                         void* vals_out, size_t n, const uint64_t* seg_offsets, size_t num_segs,
                         CodecParams prm, uint32_t cell_bits, void* temp, size_t* temp_bytes,
-                        cudaStream_t st) {
+                        cudaStream_t st, bool iota) {
     using Cell = typename C::Cell;
     constexpr bool kPairs = ValTraits<V>::kPairs;
     using VS = typename std::conditional<kPairs, V, uint32_t>::type;
@@ -329,10 +357,12 @@ rs_status run_segmented(rs_ctx* ctx, const void* keys_in, void* keys_out, const 
     a.vals_tmp = vals_tmp;
     a.n = n;
     a.seg_offsets = seg_offsets;
+    a.seg_len = seg_offsets ? 0 : n / num_segs;
     a.num_segs = num_segs;
+    a.iota = iota;
     a.order = order;
     a.ctl = ctl;
-    a.passes = std::max<uint32_t>(1, (cell_bits + RADIX_BITS - 1) / RADIX_BITS);
+    a.passes = passes_for(cell_bits);
     a.in_is_out = keys_in == keys_out;
     a.prm = prm;
     a.status = ctx->d_status;
@@ -380,24 +410,28 @@ extern "C" rs_status rs_sort_segmented(rs_ctx* ctx, rs_key_type kt, const void* 
                                        size_t* temp_bytes, rs_stream_t stream) {
     if (!ctx || !temp_bytes) return RS_ERR_INVALID;
     if (n > RS_MAX_N || num_segs > 0xfffffffeull) return RS_ERR_INVALID;
-    if (kt != RS_KEY_U32 && kt != RS_KEY_U64 && kt != RS_KEY_I64_DEC) return RS_ERR_UNSUPPORTED;
-    const size_t kbytes = kt == RS_KEY_U32 ? 4 : 8;
-    const bool pairs = vals_in != nullptr;
+    if (kt != RS_KEY_U32 && kt != RS_KEY_U64 && kt != RS_KEY_I64_DEC && kt != RS_KEY_F32 &&
+        kt != RS_KEY_F64)
+        return RS_ERR_UNSUPPORTED;
+    const size_t kbytes = (kt == RS_KEY_U32 || kt == RS_KEY_F32) ? 4 : 8;
+    const bool pairs = vals_out != nullptr;
+    const bool iota = pairs && vals_in == nullptr;
     if (pairs && val_bytes != 4 && val_bytes != 8) return RS_ERR_INVALID;
+    if (!seg_offsets && num_segs > 0 && n % num_segs) return RS_ERR_INVALID;
     if (n > 0) {
         if (!keys_in || !keys_out || (reinterpret_cast<uintptr_t>(keys_in) % kbytes) ||
             (reinterpret_cast<uintptr_t>(keys_out) % kbytes))
             return RS_ERR_INVALID;
-        if (pairs && (!vals_out || (reinterpret_cast<uintptr_t>(vals_in) % val_bytes) ||
+        if (pairs && ((reinterpret_cast<uintptr_t>(vals_in) % val_bytes) ||
                       (reinterpret_cast<uintptr_t>(vals_out) % val_bytes)))
             return RS_ERR_INVALID;
-        if (pairs && ((keys_in == keys_out) != (vals_in == vals_out))) return RS_ERR_INVALID;
+        if (pairs && !iota && ((keys_in == keys_out) != (vals_in == vals_out)))
+            return RS_ERR_INVALID;
     }
-    if (num_segs > 0 && (!seg_offsets || (reinterpret_cast<uintptr_t>(seg_offsets) % 8)))
-        return RS_ERR_INVALID;
+    if (seg_offsets && (reinterpret_cast<uintptr_t>(seg_offsets) % 8)) return RS_ERR_INVALID;
     cudaStream_t st = (cudaStream_t)stream;
     CodecParams prm{0};
-    uint32_t bits = kt == RS_KEY_U32 ? 32 : 64;
+    uint32_t bits = kbytes * 8;
     if (kt == RS_KEY_I64_DEC) {
         if (!params || params->int_digits < 0 || params->frac_digits < 0 ||
             params->int_digits + params->frac_digits < 1 ||
@@ -415,24 +449,27 @@ extern "C" rs_status rs_sort_segmented(rs_ctx* ctx, rs_key_type kt, const void* 
         if (!pairs)                                                                             \
             s = run_segmented<CODEC, NoVal>(ctx, keys_in, keys_out, nullptr, nullptr, n,        \
                                             seg_offsets, num_segs, prm, bits, temp, temp_bytes, \
-                                            st);                                                \
+                                            st, false);                                         \
         else if (val_bytes == 4)                                                                \
             s = run_segmented<CODEC, uint32_t>(ctx, keys_in, keys_out, vals_in, vals_out, n,    \
                                                seg_offsets, num_segs, prm, bits, temp,          \
-                                               temp_bytes, st);                                 \
+                                               temp_bytes, st, iota);                           \
         else                                                                                    \
             s = run_segmented<CODEC, uint64_t>(ctx, keys_in, keys_out, vals_in, vals_out, n,    \
                                                seg_offsets, num_segs, prm, bits, temp,          \
-                                               temp_bytes, st);                                 \
+                                               temp_bytes, st, iota);                           \
     } while (0)
-    if (kt == RS_KEY_U32)
-        RS_SEG_CALL(CodecU32);
-    else if (kt == RS_KEY_U64)
-        RS_SEG_CALL(CodecU64);
-    else if (2 * prm.bias <= 0xffffffffull)
-        RS_SEG_CALL(CodecDec<uint32_t>);
-    else
-        RS_SEG_CALL(CodecDec<uint64_t>);
+    switch (kt) {
+    case RS_KEY_U32: RS_SEG_CALL(CodecU32); break;
+    case RS_KEY_U64: RS_SEG_CALL(CodecU64); break;
+    case RS_KEY_F32: RS_SEG_CALL(CodecF32); break;
+    case RS_KEY_F64: RS_SEG_CALL(CodecF64); break;
+    default:
+        if (2 * prm.bias <= 0xffffffffull)
+            RS_SEG_CALL(CodecDec<uint32_t>);
+        else
+            RS_SEG_CALL(CodecDec<uint64_t>);
+    }
 #undef RS_SEG_CALL
     if (s != RS_OK && s != RS_ERR_TEMP_TOO_SMALL && s != RS_ERR_INVALID) ctx->host_error = s;
     return s;

@@ -49,6 +49,16 @@ inline Layout make_layout(size_t n, uint32_t passes, int tile, size_t cell_bytes
     return L;
 }
 
+// Digit groups of a cell index with cell_bits significant bits, rounded up
+// to an even number (never beyond the cell type's width, whose bits are a
+// multiple of 16): an in-place sort alternates buffers and so needs an even
+// count of data-moving passes, and an extra all-zero group is an identity
+// pass the plan can switch on to make the count even.
+inline uint32_t passes_for(uint32_t cell_bits) {
+    uint32_t p = std::max<uint32_t>(1, (cell_bits + RADIX_BITS - 1) / RADIX_BITS);
+    return (p + 1) & ~1u;
+}
+
 inline int count_grid(size_t n, int sms) {
     // ~16 vector loads per thread, at most 4 CTAs per SM
     const size_t per_cta = (size_t)BLOCK * 64;
@@ -75,7 +85,7 @@ rs_status run_sort(rs_ctx* ctx, const void* keys_in, void* keys_out, const void*
     constexpr bool kPairs = ValTraits<V>::kPairs;
     constexpr int IPT = ipt_for<C>();
     constexpr int TILE = BLOCK * IPT;
-    const uint32_t passes = std::max<uint32_t>(1, (cell_bits + RADIX_BITS - 1) / RADIX_BITS);
+    const uint32_t passes = passes_for(cell_bits);
     const size_t vbytes = kPairs ? sizeof(V) : 0;
     const Layout L = make_layout(n, passes, TILE, sizeof(Cell), vbytes);
 

@@ -114,8 +114,9 @@ def segment_sizes(num_segments: int = 65536, lo: int = 16, hi: int = 1 << 20,
     sizes = np.floor(np.exp(rng.uniform(np.log(lo), np.log(hi), num_segments))).astype(np.int64)
     if total is not None:
         sizes = np.maximum(np.rint(sizes * (total / sizes.sum())).astype(np.int64), 1)
-        sizes[-1] += total - sizes.sum()
-        if sizes[-1] < 1:
+        big = int(np.argmax(sizes))  # the rounding error goes to the largest segment
+        sizes[big] += total - sizes.sum()
+        if sizes[big] < 1:
             raise ValueError("total too small for the number of segments")
     return sizes
 

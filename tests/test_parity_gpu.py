@@ -205,6 +205,21 @@ def test_u64_pairs(rs, ctx, oracle):
     assert np.array_equal(from_dev(vo, np.uint32), perm.astype(np.uint32))
 
 
+@pytest.mark.parametrize("int_digits,frac_digits", [(4, 2), (1, 0), (9, 9)])
+def test_decimal_pairs_in_place(rs, ctx, oracle, int_digits, frac_digits):
+    # cells of 21, 5 and 61 bits: odd and even numbers of digit groups
+    rng = np.random.default_rng(int_digits)
+    lim = 10 ** (int_digits + frac_digits)
+    keys = rng.integers(-lim + 1, lim, 50_001).astype(np.int64)
+    vals = np.arange(keys.size, dtype=np.uint32)
+    ref_k, perm, _ = oracle.sort_fixed_decimal(keys, int_digits, frac_digits)
+    dk, dv = to_dev(keys), to_dev(vals)
+    rs.rs_sort_pairs(dk, dv, dk, dv, decimal=(int_digits, frac_digits), ctx=ctx)
+    ctx.check()
+    assert np.array_equal(from_dev(dk, np.int64), ref_k)
+    assert np.array_equal(from_dev(dv, np.uint32), perm.astype(np.uint32))
+
+
 def test_decimal_pairs(rs, ctx, oracle):
     keys = W.decimals(123_457, 6, 3)
     vals = np.arange(keys.size, dtype=np.uint32)

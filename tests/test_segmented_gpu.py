@@ -1,0 +1,161 @@
+"""Parity of rs_sort_segmented against the CPU oracle, segment by segment."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_util import from_dev, require_gpu, to_dev
+from paper_2107_01391_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rs():
+    require_gpu()
+    from paper_2107_01391_gb300 import build, binding
+    build.build()
+    return binding
+
+
+@pytest.fixture(scope="module")
+def ctx(rs):
+    c = rs.Context(0)
+    yield c
+    c.close()
+
+
+SIZES = [0, 1, 2, 17, 31, 32, 33, 255, 256, 257, 1000, 4095, 4096, 4097, 5000, 12_289, 70_000, 3, 0]
+
+
+def _offsets(sizes):
+    off = np.zeros(len(sizes) + 1, np.uint64)
+    np.cumsum(np.asarray(sizes, np.uint64), out=off[1:])
+    return off
+
+
+def _oracle_segments(oracle, keys, off, sort_fn):
+    out = np.empty_like(keys)
+    perm = np.empty(keys.size, np.int64)
+    for s in range(off.size - 1):
+        lo, hi = int(off[s]), int(off[s + 1])
+        k, p, _ = sort_fn(keys[lo:hi])
+        out[lo:hi] = k
+        perm[lo:hi] = p.astype(np.int64)
+    return out, perm
+
+
+@pytest.mark.parametrize("inplace", [False, True])
+def test_u32_pairs_mixed_sizes(rs, ctx, oracle, inplace):
+    rng = np.random.default_rng(1)
+    off = _offsets(SIZES)
+    n = int(off[-1])
+    keys = rng.integers(0, 1 << 32, n, dtype=np.uint32)
+    keys[5000:9000] = keys[5000]  # a long run of ties
+    vals = np.arange(n, dtype=np.uint32)
+    ref_k, perm = _oracle_segments(oracle, keys, off, oracle.sort_u32)
+    dk, dv, doff = to_dev(keys), to_dev(vals), to_dev(off)
+    if inplace:
+        rs.rs_sort_segmented(dk, doff, dv, dk, dv, ctx=ctx)
+        ko, vo = dk, dv
+    else:
+        ko, vo = rs.rs_sort_segmented(dk, doff, dv, ctx=ctx)
+    ctx.check()
+    assert np.array_equal(from_dev(ko, np.uint32), ref_k)
+    base = np.repeat(off[:-1].astype(np.int64), np.diff(off).astype(np.int64))
+    assert np.array_equal(from_dev(vo, np.uint32).astype(np.int64), base + perm)
+
+
+@pytest.mark.parametrize("index_dtype", [torch.int64, torch.int32])
+def test_argsort_mode(rs, ctx, oracle, index_dtype):
+    rng = np.random.default_rng(2)
+    off = _offsets(SIZES)
+    n = int(off[-1])
+    keys = rng.integers(0, 300, n, dtype=np.uint32)  # many ties
+    ref_k, perm = _oracle_segments(oracle, keys, off, oracle.sort_u32)
+    ko, idx = rs.rs_sort_segmented(to_dev(keys), to_dev(off), argsort=True,
+                                   index_dtype=index_dtype, ctx=ctx)
+    ctx.check()
+    assert np.array_equal(from_dev(ko, np.uint32), ref_k)
+    assert np.array_equal(idx.cpu().numpy().astype(np.int64), perm)
+
+
+def test_argsort_in_place_all_equal(rs, ctx):
+    keys = np.full(3 * 9000, 7, np.uint32)
+    dk = to_dev(keys)
+    ko, idx = rs.rs_sort_segmented(dk, None, keys_out=dk, num_segs=3, argsort=True, ctx=ctx)
+    ctx.check()
+    assert np.array_equal(idx.cpu().numpy(), np.tile(np.arange(9000), 3))
+
+
+def test_u64_and_decimal_keys(rs, ctx, oracle):
+    off = _offsets([5, 4096, 6000, 1, 33_333])
+    n = int(off[-1])
+    k64 = W.u64_keys(n)
+    ref, _ = _oracle_segments(oracle, k64, off, oracle.sort_u64)
+    out = rs.rs_sort_segmented(to_dev(k64), to_dev(off), ctx=ctx)
+    ctx.check()
+    assert np.array_equal(from_dev(out, np.uint64), ref)
+    dec = W.decimals(n, 6, 3)
+    ref, perm = _oracle_segments(oracle, dec, off,
+                                 lambda k: oracle.sort_fixed_decimal(k, 6, 3))
+    ko, idx = rs.rs_sort_segmented(to_dev(dec), to_dev(off), argsort=True, decimal=(6, 3), ctx=ctx)
+    ctx.check()
+    assert np.array_equal(from_dev(ko, np.int64), ref)
+    assert np.array_equal(idx.cpu().numpy(), perm)
+
+
+def test_f32_rows_vs_numpy_stable(rs, ctx):
+    rng = np.random.default_rng(3)
+    rows, length = 64, 5000
+    x = rng.standard_normal((rows, length)).astype(np.float32)
+    x[:, ::7] = np.round(x[:, ::7])  # ties
+    x[0, :4] = [0.0, -0.0, np.inf, -np.inf]
+    ko, idx = rs.rs_sort_segmented(torch.from_numpy(x).cuda().reshape(-1), None,
+                                   num_segs=rows, argsort=True, ctx=ctx)
+    ctx.check()
+    ref = np.argsort(x, axis=1, kind="stable")
+    assert np.array_equal(idx.cpu().numpy().reshape(rows, length), ref)
+    want = np.take_along_axis(x, ref, axis=1)
+    want[want == 0] = 0.0  # -0.0 is written as +0.0
+    assert np.array_equal(ko.cpu().numpy().reshape(rows, length).view(np.uint32),
+                          want.view(np.uint32))
+
+
+def test_bad_offsets_flagged(rs, ctx):
+    keys = to_dev(np.arange(100, dtype=np.uint32)[::-1].copy())
+    off = to_dev(np.array([0, 50, 40, 100], np.uint64))
+    rs.rs_sort_segmented(keys, off, ctx=ctx)
+    assert ctx.status(True) == rs.RS_ERR_RANGE
+
+
+def test_run_b_full_size(rs, ctx):
+    # 65536 segments, log-uniform sizes scaled to a total of 2^28 keys
+    sizes = W.segment_sizes(65536, total=1 << 28)
+    keys, vals, off = W.segments(sizes)
+    dk, doff = to_dev(keys), to_dev(off)
+    dv = to_dev(np.arange(keys.size, dtype=np.uint32))
+    ko, vo = rs.rs_sort_segmented(dk, doff, dv, ctx=ctx)
+    ctx.check()
+    n = keys.size
+    seg_id = torch.repeat_interleave(torch.arange(sizes.size, device="cuda"),
+                                     torch.from_numpy(sizes).cuda())
+    ki = dk.to(torch.int64) & 0xFFFFFFFF
+    kk = ko.to(torch.int64) & 0xFFFFFFFF
+    v = vo.to(torch.int64) & 0xFFFFFFFF
+    same_seg = seg_id[1:] == seg_id[:-1]
+    assert bool((kk[1:] >= kk[:-1])[same_seg].all())            # sorted within segments
+    assert bool((seg_id[v] == seg_id).all())                     # payload stays in its segment
+    seen = torch.zeros(n, dtype=torch.int32, device="cuda")
+    seen.index_fill_(0, v, 1)
+    assert int(seen.sum()) == n                                  # a permutation
+    assert bool((ki[v] == kk).all())                             # keys follow payloads
+    tie = same_seg & (kk[1:] == kk[:-1])
+    assert bool((v[1:][tie] > v[:-1][tie]).all())                # stable
+    # three segments (smallest, one tile, largest) against the oracle
+    from oracle import oracle as O
+    ko_h, vo_h = from_dev(ko, np.uint32), from_dev(vo, np.uint32)
+    for s in [int(np.argmin(sizes)), int(np.argmin(np.abs(sizes - 4096))), int(np.argmax(sizes))]:
+        lo, hi = int(off[s]), int(off[s + 1])
+        rk, rp, _ = O.sort_u32(keys[lo:hi])
+        assert np.array_equal(ko_h[lo:hi], rk)
+        assert np.array_equal(vo_h[lo:hi].astype(np.int64), lo + rp.astype(np.int64))
