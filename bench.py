@@ -52,6 +52,7 @@ def parse():
     # is not a benchmark result
     ap.add_argument("--log2n", type=int, default=28)
     ap.add_argument("--no-segmented", action="store_true")
+    ap.add_argument("--no-autograd", action="store_true")
     return ap.parse_args()
 
 
@@ -248,6 +249,43 @@ def segmented_leg(binding, ctx, steps: int, warmup: int):
             "speedup": per_call_ms / batched_ms}
 
 
+def autograd_leg(steps: int, warmup: int):
+    """Differentiable row sort: 4096 x 8192 float32 rows of distinct keys,
+    forward (sorted values + stable permutation) and backward (gradient
+    scatter), timed separately with CUDA events."""
+    import torch
+    from paper_2107_01391_gb300 import autograd, workloads as W
+    x = torch.from_numpy(W.distinct_rows(4096, 8192)).cuda()
+    g = torch.randn(4096, 8192, device="cuda")
+    stream = torch.cuda.current_stream()
+    fn = autograd.RSSortFunction
+    for _ in range(warmup):
+        xr = x.detach().requires_grad_(True)
+        vals, perm = fn.apply(xr)
+        vals.backward(g)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    fwd = bwd = 0.0
+    for _ in range(steps):
+        xr = x.detach().requires_grad_(True)
+        ev[0].record(stream)
+        vals, perm = fn.apply(xr)
+        ev[1].record(stream)
+        vals.backward(g)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        fwd += ev[0].elapsed_time(ev[1])
+        bwd += ev[1].elapsed_time(ev[2])
+    n = x.numel()
+    fwd /= steps
+    bwd /= steps
+    return {"workload": "4096 x 8192 float32 rows of distinct keys (autograd.Function)",
+            "forward_ms": fwd, "forward_keys_per_s": n / (fwd * 1e-3),
+            "backward_ms": bwd,
+            # backward reads g (4 B) and perm (8 B) and writes grad_x (4 B) per element
+            "backward_gbs": 16 * n / (bwd * 1e-3) / 1e9}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -397,6 +435,10 @@ def run_ours(args):
     if not args.no_segmented and world == 1:
         seg = segmented_leg(binding, ctx, max(1, min(args.steps, 10)), max(1, min(args.warmup, 3)))
 
+    agl = None
+    if not args.no_autograd and world == 1:
+        agl = autograd_leg(max(1, min(args.steps, 10)), max(1, min(args.warmup, 3)))
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -441,6 +483,7 @@ def run_ours(args):
                       "passes_run": r["passes_run"]} for d, r in results.items()},
         "e2e": e2e,
         "segmented": seg,
+        "autograd": agl,
         "cpu_baseline": (cpu_baseline(ORACLE_SAMPLE)
                          if world == 1 and not args.no_cpu_baseline else None),
     }

@@ -174,6 +174,20 @@ rs_status rs_sort_segmented(rs_ctx* ctx, rs_key_type kt, const void* keys_in, vo
                             const rs_key_params* params, void* temp, size_t* temp_bytes,
                             rs_stream_t stream);
 
+/* Backward of a row-wise sort: for every row r < rows and position j < cols,
+ * dst[r*cols + perm[r*cols + j]] = src[r*cols + j].  Sorting a row permutes
+ * it, so the gradient of the input is the gradient of the sorted output
+ * scattered back through the permutation (the paper has no gradient; this is
+ * the differentiable form of its output step).
+ *   src, dst    device arrays of rows*cols elements of elem_bytes (4 or 8),
+ *               not overlapping;
+ *   perm        device int64_t[rows*cols], each row a permutation of
+ *               0..cols-1 (what rs_sort_segmented's argsort output gives).
+ * An index outside [0, cols) raises RS_ERR_RANGE (device-detected) and that
+ * element is skipped. */
+rs_status rs_scatter_rows(rs_ctx* ctx, const void* src, const int64_t* perm, size_t rows,
+                          size_t cols, size_t elem_bytes, void* dst, rs_stream_t stream);
+
 /* ------------------------------------------------------- no allocation */
 
 /* The paper has no counterpart to this call; it exists for callers that
@@ -232,6 +246,15 @@ rs_status rs_ctx_set_timing(rs_ctx* ctx, int enable);
 rs_status rs_ctx_kernel_time(rs_ctx* ctx, const char* kernel_class, double* total_ms,
                              uint64_t* launches);
 rs_status rs_ctx_reset_timing(rs_ctx* ctx);
+
+/* Failure-detection check: runs the sorts' bounded look-back wait against a
+ * predecessor tile that never publishes (temp: >= 1024 device bytes, zeroed
+ * here), so the wait must give up after timeout_ns (1 ns .. 2 s), record
+ * RS_ERR_TIMEOUT in the status word and return; the context stays usable.
+ * No GPU fault is involved: the wait is a bounded poll of a word that nothing
+ * sets. */
+rs_status rs_debug_wait_timeout(rs_ctx* ctx, void* temp, size_t temp_bytes, uint64_t timeout_ns,
+                                rs_stream_t stream);
 
 /* Kernels this context launched since creation (all classes). */
 uint64_t rs_ctx_launch_count(const rs_ctx* ctx);

@@ -79,6 +79,8 @@ def _configure(lib):
     lib.oracle_sort_u64.argtypes = [p, sz, u64, p, p, st]
     lib.oracle_sort_fixed_decimal.argtypes = [p, sz, ctypes.c_int, ctypes.c_int, u64, p, p, st]
     lib.oracle_sort_strings.argtypes = [p, p, sz, ctypes.c_uint32, u64, p, st]
+    lib.oracle_sort_f64.argtypes = [p, sz, u64, p, p, st]
+    lib.oracle_sort_f64.restype = ctypes.c_int
     lib.oracle_decimal_hashing_cycle.argtypes = [p, sz, ctypes.c_int, ctypes.c_int, p,
                                                  ctypes.POINTER(ctypes.c_int), p, p, p,
                                                  ctypes.POINTER(ctypes.c_uint64)]
@@ -155,6 +157,25 @@ def sort_fixed_decimal(keys, int_digits: int, frac_digits: int, cell_cap: int = 
     _check(_load().oracle_sort_fixed_decimal(_ptr(keys), n, int_digits, frac_digits, cell_cap,
                                              _ptr(out), _ptr(perm), ctypes.byref(s)),
            "oracle_sort_fixed_decimal")
+    return out, perm, _stats(s)
+
+
+def sort_float(keys, cell_cap: int = 0, want_keys: bool = True):
+    """Stable sort of float32/float64 keys (-0.0 ties +0.0, NaN last).
+
+    float32 keys are widened to float64 first (exact and order-preserving).
+    Returns (sorted keys in the input dtype, perm, Stats).
+    """
+    keys = np.asarray(keys)
+    kd = np.ascontiguousarray(keys, dtype=np.float64)
+    n = kd.size
+    out = np.empty(n, np.float64) if want_keys else None
+    perm = np.empty(n, np.uint64)
+    s = _Stats()
+    _check(_load().oracle_sort_f64(_ptr(kd), n, cell_cap, _ptr(out), _ptr(perm), ctypes.byref(s)),
+           "oracle_sort_f64")
+    if want_keys and keys.dtype == np.float32:
+        out = keys[perm.astype(np.int64)]
     return out, perm, _stats(s)
 
 

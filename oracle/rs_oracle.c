@@ -46,6 +46,12 @@
  *     a negative key are complemented (9 - d) so raster order is value order.
  *   - Strings: one dimension per character position, radix 257, symbol 0 =
  *     past the end, byte b -> b + 1.
+ *   - Floating-point keys (not in the paper): a leading class dimension of
+ *     radix 4 (negative, zero of either sign, positive, NaN), then the 19
+ *     base-10 digits of the magnitude's IEEE-754 bit pattern read as an
+ *     integer (for finite non-negative doubles that integer grows with the
+ *     value), complemented (9 - d) for negative keys.  -0.0 ties with +0.0
+ *     and every NaN ties with every other, after all numbers.
  *   - Stability: keys are placed in input order, so equal keys keep their
  *     input order (the paper's keys-only output cannot show the difference).
  */
@@ -54,7 +60,7 @@
 #include <stdlib.h>
 #include <string.h>
 
-enum { KIND_U32 = 0, KIND_U64 = 1, KIND_DEC = 2, KIND_STR = 3 };
+enum { KIND_U32 = 0, KIND_U64 = 1, KIND_DEC = 2, KIND_STR = 3, KIND_F64 = 4 };
 
 #define MAX_DIMS 4096
 
@@ -107,6 +113,22 @@ static uint32_t digit_of(const keyspace* ks, uint64_t i, int d) {
         }
         uint32_t dig = (uint32_t)((magnitude(v) / POW10[ks->mag_digits - 1 - d]) % 10u);
         return v < 0 ? 9u - dig : dig;
+    }
+    case KIND_F64: {
+        double x = ((const double*)ks->keys)[i];
+        uint64_t bits;
+        memcpy(&bits, &x, sizeof(bits));
+        const uint64_t mag = bits & 0x7fffffffffffffffull;
+        const int is_nan = (mag >> 52) == 0x7ffull && (mag & 0xfffffffffffffull) != 0;
+        const int negative = (bits >> 63) != 0;
+        if (d == 0) {
+            if (is_nan) return 3u;
+            if (mag == 0) return 1u;
+            return negative ? 0u : 2u;
+        }
+        if (is_nan || mag == 0) return 0u;
+        uint32_t dig = (uint32_t)((mag / POW10[19 - d]) % 10u);
+        return negative ? 9u - dig : dig;
     }
     default: { /* KIND_STR */
         uint64_t beg = ks->offsets[i], len = ks->offsets[i + 1] - beg;
@@ -479,6 +501,25 @@ int oracle_sort_strings(const uint8_t* chars, const uint64_t* offsets, size_t n,
     cell_cap = effective_cap(cell_cap);
     stats_init(&st, ks, cell_cap);
     int rc = finish(ks, n, cell_cap, NULL, 0, perm_out, &st, NULL);
+    if (st_out) *st_out = st;
+    return rc;
+}
+
+int oracle_sort_f64(const double* keys, size_t n, uint64_t cell_cap, double* keys_out,
+                    uint64_t* perm_out, oracle_stats* st_out) {
+    if (n && !keys) return ORACLE_ERR_INVALID;
+    keyspace ks_storage;
+    keyspace* ks = &ks_storage;
+    memset(ks, 0, sizeof(*ks));
+    ks->kind = KIND_F64;
+    ks->keys = keys;
+    ks->D = 20; /* class + 19 magnitude digits */
+    ks->radix[0] = 4;
+    for (int d = 1; d < ks->D; d++) ks->radix[d] = 10;
+    oracle_stats st;
+    cell_cap = effective_cap(cell_cap);
+    stats_init(&st, ks, cell_cap);
+    int rc = finish(ks, n, cell_cap, keys_out, sizeof(double), perm_out, &st, NULL);
     if (st_out) *st_out = st;
     return rc;
 }

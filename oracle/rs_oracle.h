@@ -81,6 +81,13 @@ int oracle_sort_strings(const uint8_t* chars, const uint64_t* offsets, size_t n,
                         uint32_t max_len, uint64_t cell_cap, uint64_t* perm_out,
                         oracle_stats* st);
 
+/* IEEE-754 doubles (not in the paper): a class dimension (negative < zero
+ * < positive < NaN) then the 19 decimal digits of the magnitude bits,
+ * complemented for negatives.  -0.0 ties with +0.0; NaNs tie and sort last.
+ * keys_out receives the input keys in sorted order (bits unchanged). */
+int oracle_sort_f64(const double* keys, size_t n, uint64_t cell_cap, double* keys_out,
+                    uint64_t* perm_out, oracle_stats* st);
+
 /* One hashing cycle over fixed-point decimal keys whose whole digit vector
  * fits a single count array (the worked example's case), exposing the
  * paper's data structures.  radix_out (up to 32 entries) receives the shape

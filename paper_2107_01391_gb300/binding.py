@@ -404,6 +404,25 @@ def rs_sort_segmented(keys: torch.Tensor, seg_offsets: torch.Tensor | None,
     return keys_out
 
 
+def rs_scatter_rows(src: torch.Tensor, perm: torch.Tensor, out: torch.Tensor | None = None, *,
+                    ctx: Context | None = None, stream=None) -> torch.Tensor:
+    """out[r, perm[r, j]] = src[r, j] for 2-D src/perm (the backward of a row sort)."""
+    if src.dim() != 2 or perm.shape != src.shape:
+        raise ValueError("src and perm must be 2-D and of the same shape")
+    _cuda(src, "src", src.element_size(), (src.dtype,))
+    _cuda(perm, "perm", 8, (torch.int64,))
+    out = torch.empty_like(src) if out is None else out
+    ctx = ctx or default_context(src.device.index)
+    L = lib()
+    fn = L.rs_scatter_rows
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                   ctypes.c_size_t, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    _check(fn(ctx.handle, _ptr(src), _ptr(perm), src.shape[0], src.shape[1],
+              src.element_size(), _ptr(out), _stream(src, stream)), "rs_scatter_rows")
+    return out
+
+
 def rs_sort_u32_noalloc(keys: torch.Tensor, out: torch.Tensor | None = None,
                         status: torch.Tensor | None = None, *, stream=None) -> torch.Tensor:
     """The uint32 keys-only sort whose workspace is built into the library.

@@ -208,6 +208,21 @@ rs_status rs_ctx_kernel_time(rs_ctx* ctx, const char* kernel_class, double* tota
 
 uint64_t rs_ctx_launch_count(const rs_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
+rs_status rs_debug_wait_timeout(rs_ctx* ctx, void* temp, size_t temp_bytes, uint64_t timeout_ns,
+                                rs_stream_t stream) {
+    if (!ctx || !temp || temp_bytes < RADIX * sizeof(uint32_t) || timeout_ns == 0 ||
+        timeout_ns > LOOKBACK_TIMEOUT_NS || (reinterpret_cast<uintptr_t>(temp) % 4))
+        return RS_ERR_INVALID;
+    DeviceGuard dg(ctx->device);
+    if (!dg.ok) return RS_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(temp, 0, RADIX * sizeof(uint32_t), st) != cudaSuccess) return RS_ERR_CUDA;
+    wait_timeout_kernel<<<1, BLOCK, 0, st>>>(static_cast<const uint32_t*>(temp), ctx->d_status,
+                                              timeout_ns);
+    ctx->launches++;
+    return cudaGetLastError() == cudaSuccess ? RS_OK : RS_ERR_CUDA;
+}
+
 rs_status rs_sort_u32(rs_ctx* ctx, const uint32_t* keys_in, uint32_t* keys_out, size_t n,
                       void* temp, size_t* temp_bytes, rs_stream_t stream) {
     rs_status s = check_common(ctx, keys_in, keys_out, n, 4, temp_bytes);

@@ -262,7 +262,8 @@ __device__ __forceinline__ uint32_t peers_of(uint32_t d) {
 // predecessor is bounded; on expiry the status word records a timeout and the
 // partial sum is returned so that every tile still finishes.
 __device__ __forceinline__ uint32_t lookback_prefix(const uint32_t* lookback, uint32_t tile,
-                                                    uint32_t cell, uint32_t* status) {
+                                                    uint32_t cell, uint32_t* status,
+                                                    uint64_t timeout_ns = LOOKBACK_TIMEOUT_NS) {
     uint32_t before = 0;
     int64_t j = (int64_t)tile - 1;
     const uint64_t t0 = global_ns();
@@ -290,7 +291,7 @@ __device__ __forceinline__ uint32_t lookback_prefix(const uint32_t* lookback, ui
         if (done) break;
         j -= consumed;
         if (consumed == 0 && (++spins & 15u) == 0 &&
-            (global_ns() - t0 > LOOKBACK_TIMEOUT_NS || spins > LOOKBACK_MAX_POLLS)) {
+            (global_ns() - t0 > timeout_ns || spins > LOOKBACK_MAX_POLLS)) {
             atomicOr(status, STATUS_TIMEOUT);
             break;  // give up; publish what we have so successors finish
         }
@@ -491,6 +492,15 @@ __global__ void __launch_bounds__(BLOCK) fill_kernel(FillArgs a) {
         while (cell + 1 < FILL_CELLS && __ldg(&off[cell + 1]) <= j) cell++;
         __stcs(&out[j], C::encode((Cell)cell, a.prm));
     }
+}
+
+// Runs the look-back wait of tile 1 against a tile 0 that never publishes
+// (a zeroed row): every thread must give up after timeout_ns, record
+// STATUS_TIMEOUT and return.  Exercises the bounded wait without a fault.
+static __global__ void __launch_bounds__(BLOCK) wait_timeout_kernel(const uint32_t* lookback,
+                                                             uint32_t* status,
+                                                             uint64_t timeout_ns) {
+    (void)lookback_prefix(lookback, 1, threadIdx.x, status, timeout_ns);
 }
 
 }  // namespace rs

@@ -10,6 +10,7 @@ import os
 import subprocess
 import sys
 
+import numpy as np
 import pytest
 
 import test_oracle_pins as pins
@@ -39,6 +40,8 @@ MUTATIONS = {
     "hmin_never_lowered": ("} else if (ca->H_Min[2 * row + 1] > col) {",
                            "} else if (ca->H_Min[2 * row + 1] < col) {"),
     "regen_negative_not_undone": ("mag = (POW10[ks->mag_digits] - 1u) - mag;", ""),
+    "float_negatives_not_complemented": ("return negative ? 9u - dig : dig;", "return dig;"),
+    "float_nan_before_numbers": ("if (is_nan) return 3u;", "if (is_nan) return 0u;"),
     "bucket_skips_a_dimension": (
         "rc = sort_bucket(ks, items, scratch, bk[i].lo, bk[i].count, next, cell_cap, st);",
         "rc = sort_bucket(ks, items, scratch, bk[i].lo, bk[i].count, next + 1, cell_cap, st);"),
@@ -61,6 +64,8 @@ def _battery(oracle):
         ("dec_regen", lambda: pins.test_fixed_decimal_regenerates_negatives(oracle)),
         ("str_bytes", lambda: pins.test_strings_vs_python_bytes_order(oracle, 1)),
         ("invariants", lambda: pins.test_invariants_random(oracle)),
+        ("brute_float", lambda: pins.test_bruteforce_float(oracle, 3)),
+        ("float_numpy", lambda: pins.test_float_vs_numpy_stable(oracle, np.float64)),
     ]
     for name, fn in checks:
         try:

@@ -322,3 +322,32 @@ def test_stable_rank_definition(oracle):
     pos[ref] = np.arange(ref.size)
     for i in range(0, 500, 37):
         assert oracle.stable_rank(keys, i) == pos[i]
+
+
+# ------------------------------------------------------------------ floats
+
+
+def _float_reference(xs):
+    # NaN last, -0.0 == +0.0, ties in input order
+    return [i for _, _, i in sorted((bool(np.isnan(x)), 0.0 if np.isnan(x) else float(x), i)
+                                    for i, x in enumerate(xs))]
+
+
+@pytest.mark.parametrize("n", range(0, 5))
+def test_bruteforce_float(oracle, n):
+    alphabet = [-np.inf, -1.5, -0.0, 0.0, 5e-324, 2.0, np.inf, np.nan]
+    for combo in itertools.product(alphabet, repeat=n):
+        perm = oracle.sort_float(np.array(combo, np.float64))[1]
+        assert perm.tolist() == _float_reference(combo)
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_float_vs_numpy_stable(oracle, dtype):
+    rng = np.random.default_rng(12)
+    x = (rng.standard_normal(20000) * 10.0 ** rng.integers(-30, 30, 20000)).astype(dtype)
+    x[::11] = np.round(x[::11])
+    x[:8] = [0.0, -0.0, np.inf, -np.inf, np.nan, -np.nan, 1e-45, -1e-45]
+    out, perm, _ = oracle.sort_float(x)
+    ref = np.argsort(x, kind="stable")
+    assert (perm.astype(np.int64) == ref).all()
+    assert np.array_equal(out.view(np.uint8), x[ref].view(np.uint8))
