@@ -188,6 +188,29 @@ rs_status rs_sort_segmented(rs_ctx* ctx, rs_key_type kt, const void* keys_in, vo
 rs_status rs_scatter_rows(rs_ctx* ctx, const void* src, const int64_t* perm, size_t rows,
                           size_t cols, size_t elem_bytes, void* dst, rs_stream_t stream);
 
+/* The hashing cycle's data structures and the extraction cost, on the
+ * device, for fixed-point decimals whose whole digit vector fits one count
+ * array: S (one dimension per base-10 digit, Eq. 1 / Eq. 2, preceded by a
+ * radix-2 sign dimension when signed_dim != 0), the traverse maps of §3.1.3
+ * -- H_Max[row] = largest occupied last-axis coordinate, H_Min[row] =
+ * [touched flag, smallest occupied coordinate] -- and the extraction cost k
+ * of §5, the cells the extraction cycle visits walking each touched row from
+ * H_Min to H_Max.  A row is every coordinate but the last (rows = cells / 10).
+ * The sort does not need the maps (they only skip empty cells); this call
+ * reports them, e.g. k = 17 for the paper's worked example.
+ *   keys        device int64_t[n], |key| < 10^(int_digits+frac_digits);
+ *               negative keys need signed_dim (else RS_ERR_RANGE);
+ *   S_out       device uint32_t[cells] or NULL; cells = (signed_dim ? 2 : 1)
+ *               * 10^(int_digits+frac_digits) <= RS_MAX_MAP_CELLS;
+ *   hmax_out    device uint32_t[rows]; hmin_out device uint32_t[2*rows];
+ *   k_out       device uint64_t[1];
+ *   temp        workspace as for the sorts (4 bytes per row). */
+#define RS_MAX_MAP_CELLS ((uint64_t)1 << 28)
+rs_status rs_traverse_maps(rs_ctx* ctx, const int64_t* keys, size_t n, int int_digits,
+                           int frac_digits, int signed_dim, uint32_t* S_out, uint32_t* hmax_out,
+                           uint32_t* hmin_out, uint64_t* k_out, void* temp, size_t* temp_bytes,
+                           rs_stream_t stream);
+
 /* ------------------------------------------------------- no allocation */
 
 /* The paper has no counterpart to this call; it exists for callers that

@@ -423,6 +423,45 @@ def rs_scatter_rows(src: torch.Tensor, perm: torch.Tensor, out: torch.Tensor | N
     return out
 
 
+def rs_traverse_maps(keys: torch.Tensor, int_digits: int, frac_digits: int,
+                     signed_dim: bool = False, with_counts: bool = True, *,
+                     ctx: Context | None = None, stream=None):
+    """Count array S, traverse maps H_Max / H_Min and extraction cost k of the
+    paper's hashing and extraction cycles, computed on the device.
+
+    Returns (S or None, hmax [rows], hmin [rows, 2], k) as CUDA tensors (S
+    shaped like the hypercube); k is a one-element int64 tensor.
+    """
+    _cuda(keys, "keys", 8, (torch.int64,))
+    D = int_digits + frac_digits
+    cells = (2 if signed_dim else 1) * 10 ** D
+    rows = cells // 10
+    dev = keys.device
+    S = torch.empty(cells, dtype=torch.int32, device=dev) if with_counts else None
+    hmax = torch.empty(rows, dtype=torch.int32, device=dev)
+    hmin = torch.empty(rows, 2, dtype=torch.int32, device=dev)
+    k = torch.empty(1, dtype=torch.int64, device=dev)
+    ctx = ctx or default_context(dev.index)
+    L = lib()
+    fn = L.rs_traverse_maps
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_int,
+                   ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                   ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t),
+                   ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    s = _stream(keys, stream)
+    sp = _ptr(S) if S is not None else ctypes.c_void_p(0)
+
+    def call(t, b):
+        return fn(ctx.handle, _ptr(keys), keys.numel(), int_digits, frac_digits, int(signed_dim),
+                  sp, _ptr(hmax), _ptr(hmin), _ptr(k), t, b, s)
+
+    temp, tb = _workspace(call, dev, temp=None)
+    _check(call(_ptr(temp), ctypes.byref(tb)), "rs_traverse_maps")
+    shape = ((2,) if signed_dim else ()) + (10,) * D
+    return (S.view(shape) if S is not None else None), hmax, hmin, k
+
+
 def rs_sort_u32_noalloc(keys: torch.Tensor, out: torch.Tensor | None = None,
                         status: torch.Tensor | None = None, *, stream=None) -> torch.Tensor:
     """The uint32 keys-only sort whose workspace is built into the library.
