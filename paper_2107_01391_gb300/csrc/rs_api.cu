@@ -104,8 +104,6 @@ rs_status rs_ctx_create(rs_ctx** ctx, int device) {
         return RS_ERR_INVALID;
     rs_ctx* c = new rs_ctx();
     c->device = device;
-    // tuning knob for the in-tile ranking (see rs_ctx.hpp)
-    if (const char* r = std::getenv("RS_RANK")) c->rank_mode = std::strcmp(r, "match") == 0;
     DeviceGuard dg(device);
     if (!dg.ok || cudaMalloc(&c->d_area, 256) != cudaSuccess) {
         delete c;

@@ -45,7 +45,6 @@ struct rs_ctx {
     uint32_t last_passes_total = 0;
     uint32_t last_tiles = 0;
     bool timing = false;
-    int rank_mode = 0;  // 0: ballot ranking, 1: match-unit ranking (RS_RANK=match)
     std::vector<rs::TimedLaunch> timed[rs::KC_COUNT_];
     std::vector<cudaEvent_t> event_pool;
     std::mutex mu;

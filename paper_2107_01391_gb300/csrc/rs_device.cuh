@@ -169,24 +169,34 @@ __device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
 }
 
 // Lanes of the warp holding the same 8-bit digit: one ballot per bit.  Per
-// bit: sx = all ones if the bit is set (bfe.s32 sign-extends the 1-bit field),
-// bal = lanes with the bit set, and peers &= ~(bal ^ sx) in one lop3
-// (truth table 0x90 for a & ~(b ^ c) with a = 0xF0, b = 0xCC, c = 0xAA).
+// bit b: p = bit set, sx = all ones when set, bal = lanes with the bit set,
+// and peers &= ~(bal ^ sx) in one lop3 (truth table 0x90 for a & ~(b ^ c)
+// with a = 0xF0, b = 0xCC, c = 0xAA).
+template <int B>
+__device__ __forceinline__ void match_bit(uint32_t d, uint32_t& m) {
+    asm("{\n\t"
+        ".reg .pred p;\n\t"
+        ".reg .b32 t, sx, bal;\n\t"
+        "and.b32 t, %1, %2;\n\t"
+        "setp.ne.u32 p, t, 0;\n\t"
+        "selp.b32 sx, -1, 0, p;\n\t"
+        "vote.sync.ballot.b32 bal, p, 0xffffffff;\n\t"
+        "lop3.b32 %0, %0, bal, sx, 0x90;\n\t"
+        "}"
+        : "+r"(m)
+        : "r"(d), "n"(1u << B));
+}
+
 __device__ __forceinline__ uint32_t match_digit(uint32_t d) {
     uint32_t m = 0xffffffffu;
-#pragma unroll
-    for (int b = 0; b < RADIX_BITS; b++) {
-        asm("{\n\t"
-            ".reg .pred p;\n\t"
-            ".reg .b32 sx, bal;\n\t"
-            "bfe.s32 sx, %1, %2, 1;\n\t"
-            "setp.ne.s32 p, sx, 0;\n\t"
-            "vote.sync.ballot.b32 bal, p, 0xffffffff;\n\t"
-            "lop3.b32 %0, %0, bal, sx, 0x90;\n\t"
-            "}"
-            : "+r"(m)
-            : "r"(d), "r"(b));
-    }
+    match_bit<0>(d, m);
+    match_bit<1>(d, m);
+    match_bit<2>(d, m);
+    match_bit<3>(d, m);
+    match_bit<4>(d, m);
+    match_bit<5>(d, m);
+    match_bit<6>(d, m);
+    match_bit<7>(d, m);
     return m;
 }
 

@@ -42,20 +42,24 @@ struct CountArgs {
 // ----------------------------------------------------------------------------
 // Hashing cycle: count every key into each digit group's 256 cells.
 
-template <class C>
+template <class C, bool kFill>
 __device__ __forceinline__ void count_one(typename C::In key, const CountArgs& a,
                                           uint32_t (*sh)[RADIX], uint32_t* sfill, bool& ok,
                                           bool& big) {
     using Cell = typename C::Cell;
     const Cell cell = C::decode(key, a.prm, ok);
+    // every byte of the cell is counted (a group beyond the key's passes is
+    // never read by the plan); unrolled, no per-group test
 #pragma unroll
-    for (uint32_t p = 0; p < sizeof(Cell); p++)  // one 8-bit group per cell byte
-        if (p < a.passes) atomicAdd(&sh[p][digit_of(cell, p * RADIX_BITS)], 1u);
-    if (a.fill_allowed && !big) {
-        if (cell < (Cell)FILL_CELLS)
-            atomicAdd(&sfill[(uint32_t)cell], 1u);
-        else
-            big = true;
+    for (uint32_t p = 0; p < sizeof(Cell); p++)
+        atomicAdd(&sh[p][digit_of(cell, p * RADIX_BITS)], 1u);
+    if constexpr (kFill) {
+        if (!big) {
+            if (cell < (Cell)FILL_CELLS)
+                atomicAdd(&sfill[(uint32_t)cell], 1u);
+            else
+                big = true;
+        }
     }
 }
 
@@ -137,52 +141,68 @@ static __device__ void make_plan(const CountArgs& a, uint32_t* s_warp) {
     }
 }
 
-template <class C>
+template <class C, bool kFill>
 __global__ void __launch_bounds__(BLOCK) count_kernel(CountArgs a) {
     using In = typename C::In;
     if (a.skip && *a.skip) return;  // the plan stays zeroed: every pass inactive
     __shared__ uint32_t sh[MAX_PASSES][RADIX];
-    __shared__ uint32_t sfill[FILL_CELLS];
+    __shared__ uint32_t sfill[kFill ? FILL_CELLS : 1];
     __shared__ uint32_t s_warp[WARPS];
     __shared__ uint32_t s_last;
     const uint32_t t = threadIdx.x;
     for (uint32_t i = t; i < MAX_PASSES * RADIX; i += BLOCK) (&sh[0][0])[i] = 0;
-    if (a.fill_allowed)
+    if constexpr (kFill)
         for (uint32_t i = t; i < FILL_CELLS; i += BLOCK) sfill[i] = 0;
     __syncthreads();
 
     const In* keys = static_cast<const In*>(a.keys_in);
     bool ok = true;
-    bool big = a.fill_allowed ? (__ldcg(&a.plan->fill_impossible) != 0) : true;
-    // 16-byte vector body with a scalar head and tail.
+    bool big = kFill ? (__ldcg(&a.plan->fill_impossible) != 0) : true;
+    // 16-byte vector body with a scalar head and tail; n < 2^30, so 32-bit
+    // indices suffice
     constexpr uint32_t VEC = 16 / sizeof(In);
+    const uint32_t n = (uint32_t)a.n;
     const uintptr_t addr = reinterpret_cast<uintptr_t>(keys);
-    uint64_t head = ((16 - (addr & 15)) & 15) / sizeof(In);
-    if (head > a.n) head = a.n;
-    const uint64_t nvec = (a.n - head) / VEC;
-    const uint64_t tail0 = head + nvec * VEC;
-    const uint64_t gtid = (uint64_t)blockIdx.x * BLOCK + t;
-    const uint64_t gsize = (uint64_t)gridDim.x * BLOCK;
-    if (gtid < head) count_one<C>(keys[gtid], a, sh, sfill, ok, big);
+    uint32_t head = (uint32_t)(((16 - (addr & 15)) & 15) / sizeof(In));
+    if (head > n) head = n;
+    const uint32_t nvec = (n - head) / VEC;
+    const uint32_t tail0 = head + nvec * VEC;
+    const uint32_t gtid = blockIdx.x * BLOCK + t;
+    const uint32_t gsize = gridDim.x * BLOCK;
+    if (gtid < head) count_one<C, kFill>(keys[gtid], a, sh, sfill, ok, big);
     const uint4* vkeys = reinterpret_cast<const uint4*>(keys + head);
-    for (uint64_t v = gtid; v < nvec; v += gsize) {
+    // four independent 16-byte loads in flight per thread before counting
+    uint32_t v = gtid;
+    for (; v + 3 * gsize < nvec; v += 4 * gsize) {
+        uint4 q[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) q[u] = __ldg(&vkeys[v + u * gsize]);
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const In* e = reinterpret_cast<const In*>(&q[u]);
+#pragma unroll
+            for (uint32_t j = 0; j < VEC; j++) count_one<C, kFill>(e[j], a, sh, sfill, ok, big);
+        }
+    }
+    for (; v < nvec; v += gsize) {
         const uint4 q = __ldg(&vkeys[v]);
         const In* e = reinterpret_cast<const In*>(&q);
 #pragma unroll
-        for (uint32_t j = 0; j < VEC; j++) count_one<C>(e[j], a, sh, sfill, ok, big);
+        for (uint32_t j = 0; j < VEC; j++) count_one<C, kFill>(e[j], a, sh, sfill, ok, big);
     }
-    if (tail0 + gtid < a.n) count_one<C>(keys[tail0 + gtid], a, sh, sfill, ok, big);
+    if (tail0 + gtid < n) count_one<C, kFill>(keys[tail0 + gtid], a, sh, sfill, ok, big);
     if (!ok) atomicOr(a.status, STATUS_RANGE);
-    if (a.fill_allowed && big) a.plan->fill_impossible = 1;
+    if (kFill && big) a.plan->fill_impossible = 1;
     __syncthreads();
 
     for (uint32_t i = t; i < a.passes * RADIX; i += BLOCK) {
         const uint32_t c = (&sh[0][0])[i];
         if (c) atomicAdd(&a.hist[i], c);
     }
-    if (a.fill_allowed && __ldcg(&a.plan->fill_impossible) == 0) {
-        for (uint32_t i = t; i < FILL_CELLS; i += BLOCK)
-            if (sfill[i]) atomicAdd(&a.fill_hist[i], sfill[i]);
+    if constexpr (kFill) {
+        if (__ldcg(&a.plan->fill_impossible) == 0)
+            for (uint32_t i = t; i < FILL_CELLS; i += BLOCK)
+                if (sfill[i]) atomicAdd(&a.fill_hist[i], sfill[i]);
     }
     __threadfence();
     __syncthreads();
@@ -244,18 +264,6 @@ __device__ __forceinline__ void* pick_dst(const PassArgs& a, uint32_t b, bool va
     return vals ? a.vals_out : a.keys_out;
 }
 
-// Peers of this lane's digit in the warp: RANK_BALLOT builds the mask from one
-// ballot per digit bit, RANK_MATCH asks the hardware match unit.
-enum : int { RANK_BALLOT = 0, RANK_MATCH = 1 };
-
-template <int RANK>
-__device__ __forceinline__ uint32_t peers_of(uint32_t d) {
-    if constexpr (RANK == RANK_MATCH)
-        return __match_any_sync(0xffffffffu, d);
-    else
-        return match_digit(d);
-}
-
 // Decoupled look-back for one cell: the sum of this cell's counts over all
 // tiles before `tile`, walking back four predecessors per round trip until a
 // tile that already holds its inclusive prefix.  The wait for an unpublished
@@ -299,8 +307,9 @@ __device__ __forceinline__ uint32_t lookback_prefix(const uint32_t* lookback, ui
     return before;
 }
 
-template <class C, typename V, int IPT, int RANK>
-__global__ void __launch_bounds__(BLOCK) pass_kernel(PassArgs a) {
+template <class C, typename V, int IPT>
+__global__ void __launch_bounds__(BLOCK, sizeof(typename C::Cell) == 4 ? 4 : 2)
+    pass_kernel(PassArgs a) {
     using Cell = typename C::Cell;
     using In = typename C::In;
     using Out = typename C::Out;
@@ -308,9 +317,9 @@ __global__ void __launch_bounds__(BLOCK) pass_kernel(PassArgs a) {
     constexpr int TILE = BLOCK * IPT;
     using VS = typename std::conditional<kPairs, V, uint32_t>::type;  // storage type
 
-    // wh[w][d]: first the count of cell d in warp w's slice, then the
+    // ws[w][d]: first the count of cell d in warp w's slice, then the
     // tile-local position where warp w's next key of cell d goes
-    __shared__ uint32_t wh[WARPS][RADIX];
+    __shared__ uint32_t ws[WARPS][RADIX];
     __shared__ uint32_t s_bin_global[RADIX];  // global position of tile-local index 0 per cell
     __shared__ uint32_t s_warp[WARPS];
     __shared__ uint32_t s_tile;
@@ -330,7 +339,7 @@ __global__ void __launch_bounds__(BLOCK) pass_kernel(PassArgs a) {
     const bool last = P->last_active == a.pass;
 
     if (t == 0) s_tile = atomicAdd(a.tile_counter, 1u);
-    for (uint32_t d = lane; d < RADIX; d += 32) wh[warp][d] = 0;
+    for (uint32_t d = lane; d < RADIX; d += 32) ws[warp][d] = 0;
     __syncthreads();
     const uint32_t tile = s_tile;
     const uint64_t tile_base = (uint64_t)tile * TILE;
@@ -376,15 +385,15 @@ __global__ void __launch_bounds__(BLOCK) pass_kernel(PassArgs a) {
 
     // ---- counts per (warp, cell): order does not matter here ----
 #pragma unroll
-    for (int i = 0; i < IPT; i++) atomicAdd(&wh[warp][digit_of(k[i], a.shift)], 1u);
+    for (int i = 0; i < IPT; i++) atomicAdd(&ws[warp][digit_of(k[i], a.shift)], 1u);
     __syncthreads();
 
     // ---- tile count per cell, publish it, then tile-local starts ----
     uint32_t run = 0;
 #pragma unroll
     for (int w = 0; w < WARPS; w++) {
-        const uint32_t x = wh[w][t];
-        wh[w][t] = run;
+        const uint32_t x = ws[w][t];
+        ws[w][t] = run;
         run += x;
     }
     // padding items carry cell ~0 (digit 255) and sit after every real item
@@ -394,7 +403,7 @@ __global__ void __launch_bounds__(BLOCK) pass_kernel(PassArgs a) {
     uint32_t tile_total;
     const uint32_t excl = block_exclusive_scan(count, s_warp, &tile_total);
 #pragma unroll
-    for (int w = 0; w < WARPS; w++) wh[w][t] += excl;
+    for (int w = 0; w < WARPS; w++) ws[w][t] += excl;
     __syncthreads();
 
     // ---- stable rank in (cell, input) order, scattered into shared memory ----
@@ -402,13 +411,13 @@ __global__ void __launch_bounds__(BLOCK) pass_kernel(PassArgs a) {
 #pragma unroll
     for (int i = 0; i < IPT; i++) {
         const uint32_t d = digit_of(k[i], a.shift);
-        const uint32_t peers = peers_of<RANK>(d);
-        // every lane reads its cell's running position; the highest peer
-        // (the last of them in input order) advances it past the group
-        uint32_t* slot = &wh[warp][d];
+        const uint32_t peers = match_digit(d);
+        uint32_t* slot = &ws[warp][d];
         const uint32_t at = *slot;
         const uint32_t below = __popc(peers & lt);
-        __syncwarp();  // every peer has read the slot before it moves
+        // every peer has read the slot before the highest one (the last of
+        // them in input order) moves it past the group
+        __syncwarp();
         if ((peers & gt) == 0) *slot = at + below + 1;
         const uint32_t pos = at + below;
         s_keys[pos] = k[i];

@@ -107,7 +107,7 @@ extern "C" rs_status rs_sort_u32_noalloc(const uint32_t* keys_in, uint32_t* keys
     a.fill_offsets = fill_offsets;
     a.status = status_word;
     a.info = info;
-    count_kernel<C><<<count_grid(n, sm_count(device)), BLOCK, 0, st>>>(a);
+    count_kernel<C, true><<<count_grid(n, sm_count(device)), BLOCK, 0, st>>>(a);
 
     FillArgs f{};
     f.keys_out = keys_out;
@@ -134,7 +134,7 @@ extern "C" rs_status rs_sort_u32_noalloc(const uint32_t* keys_in, uint32_t* keys
         pa.lookback_next = lb[(p + 1) & 1];
         pa.tile_counter = &plan->tile_counter[p];
         pa.status = status_word;
-        pass_kernel<C, NoVal, IPT, RANK_BALLOT><<<(unsigned)L.tiles, BLOCK, Smem::kBytes, st>>>(pa);
+        pass_kernel<C, NoVal, IPT><<<(unsigned)L.tiles, BLOCK, Smem::kBytes, st>>>(pa);
     }
     return cudaGetLastError() == cudaSuccess ? RS_OK : RS_ERR_CUDA;
 }

@@ -60,10 +60,10 @@ inline uint32_t passes_for(uint32_t cell_bits) {
 }
 
 inline int count_grid(size_t n, int sms) {
-    // ~16 vector loads per thread, at most 4 CTAs per SM
+    // at least 64 keys per thread, at most 8 CTAs per SM (full occupancy)
     const size_t per_cta = (size_t)BLOCK * 64;
     size_t g = (n + per_cta - 1) / per_cta;
-    g = std::max<size_t>(1, std::min<size_t>(g, (size_t)sms * 4));
+    g = std::max<size_t>(1, std::min<size_t>(g, (size_t)sms * 8));
     return (int)g;
 }
 
@@ -129,7 +129,11 @@ rs_status run_sort(rs_ctx* ctx, const void* keys_in, void* keys_out, const void*
         a.info = static_cast<DevInfo*>(ctx->d_info);
         a.skip = skip;
         LaunchTimer lt(ctx, KC_HIST, stream);
-        count_kernel<C><<<count_grid(n, sm_count(ctx->device)), BLOCK, 0, stream>>>(a);
+        const int grid = count_grid(n, sm_count(ctx->device));
+        if (fill_allowed)
+            count_kernel<C, true><<<grid, BLOCK, 0, stream>>>(a);
+        else
+            count_kernel<C, false><<<grid, BLOCK, 0, stream>>>(a);
     }
     if (fill_allowed) {
         FillArgs f{};
@@ -144,16 +148,12 @@ rs_status run_sort(rs_ctx* ctx, const void* keys_in, void* keys_out, const void*
         fill_kernel<C><<<grid, BLOCK, 0, stream>>>(f);
     }
     using Smem = PassSmem<Cell, V, IPT>;
-    auto kern_ballot = pass_kernel<C, V, IPT, RANK_BALLOT>;
-    auto kern_match = pass_kernel<C, V, IPT, RANK_MATCH>;
-    auto kern = ctx->rank_mode == RANK_MATCH ? kern_match : kern_ballot;
+    auto kern = pass_kernel<C, V, IPT>;
     // static + dynamic shared memory may exceed the 48 KB default: opt in
     // once per device for this instantiation
     static bool smem_set[64] = {};
     if (ctx->device < 64 && !smem_set[ctx->device]) {
-        if (cudaFuncSetAttribute(kern_ballot, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)Smem::kBytes) != cudaSuccess ||
-            cudaFuncSetAttribute(kern_match, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)Smem::kBytes) != cudaSuccess)
             return RS_ERR_CUDA;
         smem_set[ctx->device] = true;
