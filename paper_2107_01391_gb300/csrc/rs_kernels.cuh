@@ -21,6 +21,8 @@
 
 namespace rs {
 
+constexpr int LOOKBACK_WINDOW = 4;  // predecessor words loaded per round trip (4, 8, 16 measured: 4 best)
+
 struct CountArgs {
     const void* keys_in;
     uint64_t n;
@@ -265,8 +267,8 @@ __device__ __forceinline__ void* pick_dst(const PassArgs& a, uint32_t b, bool va
 }
 
 // Decoupled look-back for one cell: the sum of this cell's counts over all
-// tiles before `tile`, walking back four predecessors per round trip until a
-// tile that already holds its inclusive prefix.  The wait for an unpublished
+// tiles before `tile`, walking back LOOKBACK_WINDOW predecessors per round
+// trip until a tile that already holds its inclusive prefix.  The wait for an unpublished
 // predecessor is bounded; on expiry the status word records a timeout and the
 // partial sum is returned so that every tile still finishes.
 __device__ __forceinline__ uint32_t lookback_prefix(const uint32_t* lookback, uint32_t tile,
@@ -277,15 +279,15 @@ __device__ __forceinline__ uint32_t lookback_prefix(const uint32_t* lookback, ui
     const uint64_t t0 = global_ns();
     uint32_t spins = 0;
     while (j >= 0) {
-        uint32_t s[4];
+        uint32_t s[LOOKBACK_WINDOW];
 #pragma unroll
-        for (int q = 0; q < 4; q++)
+        for (int q = 0; q < LOOKBACK_WINDOW; q++)
             s[q] = j - q >= 0 ? ld_relaxed(&lookback[(uint64_t)(j - q) * RADIX + cell])
                               : LB_INCLUSIVE;
         int consumed = 0;
         bool done = false, blocked = false;
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
+        for (int q = 0; q < LOOKBACK_WINDOW; q++) {
             if (done || blocked) continue;
             const uint32_t flag = s[q] & ~LB_VALUE;
             if (flag == 0) {
@@ -308,7 +310,7 @@ __device__ __forceinline__ uint32_t lookback_prefix(const uint32_t* lookback, ui
 }
 
 template <class C, typename V, int IPT>
-__global__ void __launch_bounds__(BLOCK, sizeof(typename C::Cell) == 4 ? 4 : 2)
+__global__ void __launch_bounds__(BLOCK, sizeof(typename C::Cell) == 4 ? 3 : 2)
     pass_kernel(PassArgs a) {
     using Cell = typename C::Cell;
     using In = typename C::In;
@@ -426,6 +428,7 @@ __global__ void __launch_bounds__(BLOCK, sizeof(typename C::Cell) == 4 ? 4 : 2)
     }
 
     // ---- decoupled look-back: this cell's count in all earlier tiles ----
+    // (after the ranking: the predecessors publish while this tile ranks)
     uint32_t before = 0;
     if (tile > 0) {
         before = lookback_prefix(a.lookback, tile, t, a.status);

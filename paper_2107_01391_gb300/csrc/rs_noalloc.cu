@@ -67,7 +67,7 @@ extern "C" rs_status rs_sort_u32_noalloc(const uint32_t* keys_in, uint32_t* keys
     if (n == 0) return RS_OK;
 
     using C = CodecU32;
-    constexpr int IPT = ipt_for<C>();
+    constexpr int IPT = ipt_for<C, NoVal>();
     constexpr int TILE = BLOCK * IPT;
     constexpr uint32_t passes = 4;
     const Layout L = make_layout(n, passes, TILE, sizeof(uint32_t), 0);

@@ -18,9 +18,12 @@ namespace rs {
 
 inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 
-template <class C>
+// Keys per thread of a pass tile (256 threads).  For 32-bit cells 24 was
+// measured best on GB300 (12, 16, 20, 24, 28 tried; 3 CTAs per SM): larger
+// tiles amortise the per-tile scan, barriers and look-back.
+template <class C, typename V>
 constexpr int ipt_for() {
-    return sizeof(typename C::Cell) == 4 ? 16 : 12;
+    return sizeof(typename C::Cell) == 4 ? (ValTraits<V>::kPairs && sizeof(V) > 4 ? 16 : 24) : 12;
 }
 
 struct Layout {
@@ -83,7 +86,7 @@ rs_status run_sort(rs_ctx* ctx, const void* keys_in, void* keys_out, const void*
                    size_t* temp_bytes, cudaStream_t stream, const uint32_t* skip) {
     using Cell = typename C::Cell;
     constexpr bool kPairs = ValTraits<V>::kPairs;
-    constexpr int IPT = ipt_for<C>();
+    constexpr int IPT = ipt_for<C, V>();
     constexpr int TILE = BLOCK * IPT;
     const uint32_t passes = passes_for(cell_bits);
     const size_t vbytes = kPairs ? sizeof(V) : 0;

@@ -1,6 +1,6 @@
 """Parity of the CUDA path against the CPU oracle, element by element.
 
-Sizes span several tiles (4096 keys for 32-bit cells, 3072 for 64-bit) with
+Sizes span several tiles (6144 keys for 32-bit cells, 3072 for 64-bit) with
 ragged tails; every comparison is bit-exact (keys, and payload order for
 pairs).  All calls go through the C ABI via the thin binding.
 """
@@ -13,7 +13,8 @@ from paper_2107_01391_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-SIZES_U32 = [1, 2, 3, 31, 4095, 4096, 4097, 3 * 4096 + 17, 100_003]
+# pass tiles hold 6144 keys (32-bit cells) or 3072 (64-bit cells)
+SIZES_U32 = [1, 2, 3, 31, 4095, 4097, 6143, 6144, 6145, 3 * 6144 + 17, 100_003]
 
 
 @pytest.fixture(scope="module")
