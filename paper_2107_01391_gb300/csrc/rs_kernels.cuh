@@ -44,17 +44,33 @@ struct CountArgs {
 // ----------------------------------------------------------------------------
 // Hashing cycle: count every key into each digit group's 256 cells.
 
+// Shared-memory counts of 32-bit cells without bank conflicts: each lane owns
+// a private copy of every counter, packed as 16-bit halves (cells d and d^1
+// share a word), and lane l's copies all sit in bank l.  Word index of
+// (group g, cell d, lane l): ((g * RADIX/2 + d/2) * 32 + l); half = d & 1.
+// A CTA counts fewer than 32 * 65535 keys per lane copy (n < 2^30 over at
+// least min(n / 16384, 8 per SM) CTAs), so the halves cannot overflow.
+constexpr uint32_t LANE_HIST_WORDS = 4 * (RADIX / 2) * 32;  // four groups of a 32-bit cell
+
 template <class C, bool kFill>
 __device__ __forceinline__ void count_one(typename C::In key, const CountArgs& a,
-                                          uint32_t (*sh)[RADIX], uint32_t* sfill, bool& ok,
-                                          bool& big) {
+                                          uint32_t (*sh)[RADIX], uint32_t* lh, uint32_t lane,
+                                          uint32_t* sfill, bool& ok, bool& big) {
     using Cell = typename C::Cell;
     const Cell cell = C::decode(key, a.prm, ok);
     // every byte of the cell is counted (a group beyond the key's passes is
     // never read by the plan); unrolled, no per-group test
+    if constexpr (sizeof(Cell) == 4) {
 #pragma unroll
-    for (uint32_t p = 0; p < sizeof(Cell); p++)
-        atomicAdd(&sh[p][digit_of(cell, p * RADIX_BITS)], 1u);
+        for (uint32_t p = 0; p < 4; p++) {
+            const uint32_t d = digit_of(cell, p * RADIX_BITS);
+            atomicAdd(&lh[((p * (RADIX / 2) + (d >> 1)) << 5) + lane], 1u << ((d & 1u) << 4));
+        }
+    } else {
+#pragma unroll
+        for (uint32_t p = 0; p < sizeof(Cell); p++)
+            atomicAdd(&sh[p][digit_of(cell, p * RADIX_BITS)], 1u);
+    }
     if constexpr (kFill) {
         if (!big) {
             if (cell < (Cell)FILL_CELLS)
@@ -147,12 +163,17 @@ template <class C, bool kFill>
 __global__ void __launch_bounds__(BLOCK) count_kernel(CountArgs a) {
     using In = typename C::In;
     if (a.skip && *a.skip) return;  // the plan stays zeroed: every pass inactive
+    using Cell = typename C::Cell;
+    constexpr bool kLaneHist = sizeof(Cell) == 4;
     __shared__ uint32_t sh[MAX_PASSES][RADIX];
     __shared__ uint32_t sfill[kFill ? FILL_CELLS : 1];
     __shared__ uint32_t s_warp[WARPS];
     __shared__ uint32_t s_last;
-    const uint32_t t = threadIdx.x;
+    extern __shared__ uint32_t lh[];  // LANE_HIST_WORDS when kLaneHist
+    const uint32_t t = threadIdx.x, lane = lane_id();
     for (uint32_t i = t; i < MAX_PASSES * RADIX; i += BLOCK) (&sh[0][0])[i] = 0;
+    if constexpr (kLaneHist)
+        for (uint32_t i = t; i < LANE_HIST_WORDS; i += BLOCK) lh[i] = 0;
     if constexpr (kFill)
         for (uint32_t i = t; i < FILL_CELLS; i += BLOCK) sfill[i] = 0;
     __syncthreads();
@@ -171,7 +192,7 @@ __global__ void __launch_bounds__(BLOCK) count_kernel(CountArgs a) {
     const uint32_t tail0 = head + nvec * VEC;
     const uint32_t gtid = blockIdx.x * BLOCK + t;
     const uint32_t gsize = gridDim.x * BLOCK;
-    if (gtid < head) count_one<C, kFill>(keys[gtid], a, sh, sfill, ok, big);
+    if (gtid < head) count_one<C, kFill>(keys[gtid], a, sh, lh, lane, sfill, ok, big);
     const uint4* vkeys = reinterpret_cast<const uint4*>(keys + head);
     // four independent 16-byte loads in flight per thread before counting
     uint32_t v = gtid;
@@ -183,19 +204,39 @@ __global__ void __launch_bounds__(BLOCK) count_kernel(CountArgs a) {
         for (int u = 0; u < 4; u++) {
             const In* e = reinterpret_cast<const In*>(&q[u]);
 #pragma unroll
-            for (uint32_t j = 0; j < VEC; j++) count_one<C, kFill>(e[j], a, sh, sfill, ok, big);
+            for (uint32_t j = 0; j < VEC; j++) count_one<C, kFill>(e[j], a, sh, lh, lane, sfill, ok, big);
         }
     }
     for (; v < nvec; v += gsize) {
         const uint4 q = __ldg(&vkeys[v]);
         const In* e = reinterpret_cast<const In*>(&q);
 #pragma unroll
-        for (uint32_t j = 0; j < VEC; j++) count_one<C, kFill>(e[j], a, sh, sfill, ok, big);
+        for (uint32_t j = 0; j < VEC; j++) count_one<C, kFill>(e[j], a, sh, lh, lane, sfill, ok, big);
     }
-    if (tail0 + gtid < n) count_one<C, kFill>(keys[tail0 + gtid], a, sh, sfill, ok, big);
+    if (tail0 + gtid < n) count_one<C, kFill>(keys[tail0 + gtid], a, sh, lh, lane, sfill, ok, big);
     if (!ok) atomicOr(a.status, STATUS_RANGE);
     if (kFill && big) a.plan->fill_impossible = 1;
     __syncthreads();
+    if constexpr (kLaneHist) {
+        // fold the 32 lane copies: one row (group, cell pair) per warp step,
+        // lane l reads the copy in bank l, a warp sum per 16-bit half
+        const uint32_t warp = t >> 5;
+        for (uint32_t row = warp; row < 4 * (RADIX / 2); row += WARPS) {
+            const uint32_t w = lh[(row << 5) + lane];
+            uint32_t lo = w & 0xffffu, hi = w >> 16;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                lo += __shfl_xor_sync(0xffffffffu, lo, o);
+                hi += __shfl_xor_sync(0xffffffffu, hi, o);
+            }
+            if (lane == 0) {
+                const uint32_t g = row / (RADIX / 2), d = (row % (RADIX / 2)) * 2;
+                sh[g][d] = lo;
+                sh[g][d + 1] = hi;
+            }
+        }
+        __syncthreads();
+    }
 
     for (uint32_t i = t; i < a.passes * RADIX; i += BLOCK) {
         const uint32_t c = (&sh[0][0])[i];

@@ -107,7 +107,11 @@ extern "C" rs_status rs_sort_u32_noalloc(const uint32_t* keys_in, uint32_t* keys
     a.fill_offsets = fill_offsets;
     a.status = status_word;
     a.info = info;
-    count_kernel<C, true><<<count_grid(n, sm_count(device)), BLOCK, 0, st>>>(a);
+    constexpr size_t lane_hist = LANE_HIST_WORDS * sizeof(uint32_t);
+    if (cudaFuncSetAttribute(count_kernel<C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)lane_hist) != cudaSuccess)
+        return RS_ERR_CUDA;
+    count_kernel<C, true><<<count_grid(n, sm_count(device)), BLOCK, lane_hist, st>>>(a);
 
     FillArgs f{};
     f.keys_out = keys_out;

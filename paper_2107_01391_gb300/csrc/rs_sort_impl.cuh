@@ -62,12 +62,16 @@ inline uint32_t passes_for(uint32_t cell_bits) {
     return (p + 1) & ~1u;
 }
 
-inline int count_grid(size_t n, int sms) {
-    // at least 64 keys per thread, at most 8 CTAs per SM (full occupancy)
+inline int count_grid(size_t n, int sms, int per_sm = 8) {
+    // at least 64 keys per thread, at most per_sm CTAs per SM (8 measured
+    // best at 2^28 keys, 3 resident at a time with 64 KB of lane counters),
+    // and at most 2^21 keys per CTA so that the 16-bit lane counters of
+    // count_kernel (32 lanes x 65535) cannot overflow
     const size_t per_cta = (size_t)BLOCK * 64;
     size_t g = (n + per_cta - 1) / per_cta;
-    g = std::max<size_t>(1, std::min<size_t>(g, (size_t)sms * 8));
-    return (int)g;
+    g = std::min<size_t>(g, (size_t)sms * per_sm);
+    g = std::max<size_t>(g, (n + (1u << 21) - 1) >> 21);
+    return (int)std::max<size_t>(g, 1);
 }
 
 inline int sm_count(int device) {
@@ -132,11 +136,23 @@ rs_status run_sort(rs_ctx* ctx, const void* keys_in, void* keys_out, const void*
         a.info = static_cast<DevInfo*>(ctx->d_info);
         a.skip = skip;
         LaunchTimer lt(ctx, KC_HIST, stream);
+        const size_t lane_hist = sizeof(Cell) == 4 ? LANE_HIST_WORDS * sizeof(uint32_t) : 0;
         const int grid = count_grid(n, sm_count(ctx->device));
+        static bool count_smem_set[64] = {};
+        if (lane_hist && ctx->device < 64 && !count_smem_set[ctx->device]) {
+            if (cudaFuncSetAttribute(count_kernel<C, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)lane_hist) != cudaSuccess ||
+                cudaFuncSetAttribute(count_kernel<C, false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)lane_hist) != cudaSuccess)
+                return RS_ERR_CUDA;
+            count_smem_set[ctx->device] = true;
+        }
         if (fill_allowed)
-            count_kernel<C, true><<<grid, BLOCK, 0, stream>>>(a);
+            count_kernel<C, true><<<grid, BLOCK, lane_hist, stream>>>(a);
         else
-            count_kernel<C, false><<<grid, BLOCK, 0, stream>>>(a);
+            count_kernel<C, false><<<grid, BLOCK, lane_hist, stream>>>(a);
     }
     if (fill_allowed) {
         FillArgs f{};
