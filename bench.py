@@ -56,6 +56,30 @@ def parse():
     return ap.parse_args()
 
 
+def workload_config(n: int, dist_name: str, world: int, passes: int = 4) -> dict:
+    """The `config` object shared by both arms of the benchmark."""
+    return {
+        "workload": "2^28 u32 keys + u32 index payload (stable pairs sort), "
+                    f"{dist_name} over [0,2^32)",
+        "n": n, "key": "u32", "value": "u32 index", "dist": dist_name,
+        "parallelism": f"replicas x{world}",
+        "l2": "inputs (2 GiB of keys+values) larger than the 129 MB L2; no flush",
+        "digit_bits": 8, "passes": passes,
+        "alg_bytes_per_key": COUNT_BYTES_PER_KEY + PASS_BYTES_PER_KEY * passes,
+    }
+
+
+def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
+    """The slowest rank's time: all-reduce MAX over the process group."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -306,8 +330,8 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": "2^28 u32 keys + u32 index payload, uniform over [0,2^32)",
-                   "n": N_KEYS, "step_sample": REFERENCE_STEP_SAMPLE},
+        "config": dict(workload_config(N_KEYS, "uniform", world),
+                       step_sample=REFERENCE_STEP_SAMPLE),
         "cpu_baseline": {"value": value, "unit": "keys/s", "cores": 1, "kind": "oracle",
                          "sample": f"each step sorts the first {REFERENCE_STEP_SAMPLE} keys "
                                    "of the workload with the single-threaded oracle"},
@@ -340,12 +364,6 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
 
     results = {}
     for dname in dists:
@@ -376,7 +394,7 @@ def run_ours(args):
             sampler.__exit__(None, None, None)
         ctx.set_timing(False)
         ctx.check()
-        ms = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+        ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
         pass_ms, pass_launches = ctx.kernel_time("pass")
         count_ms, count_launches = ctx.kernel_time("hist")
         plan = ctx.last_plan()
@@ -394,42 +412,68 @@ def run_ours(args):
         del dk, dv, ko, vo, temp
         torch.cuda.empty_cache()
 
-    # end to end through the C ABI: pinned host keys+values in, sorted out
+    # end to end through the C ABI: pinned host keys+values in, sorted keys
+    # and values back to pinned host memory, every step.  Steps are pipelined
+    # over three streams with two buffer sets: while step i sorts, step i+1's
+    # inputs go up and step i-1's results come back (both copy directions
+    # run at once).
     e2e = None
     if not args.no_e2e:
         keys_h, vals_h = W.u32_pairs(n, dists[0], seed_extra=rank)
         hk = torch.from_numpy(keys_h.view(np.int32)).pin_memory()
         hv = torch.from_numpy(vals_h.view(np.int32)).pin_memory()
-        ok_h, ov_h = torch.empty_like(hk).pin_memory(), torch.empty_like(hv).pin_memory()
-        dk, dv = torch.empty(n, dtype=torch.int32, device="cuda"), torch.empty(
-            n, dtype=torch.int32, device="cuda")
-        ko, vo = torch.empty_like(dk), torch.empty_like(dv)
+        out_h = [(torch.empty_like(hk).pin_memory(), torch.empty_like(hv).pin_memory())
+                 for _ in range(2)]
+        dev = [tuple(torch.empty(n, dtype=torch.int32, device="cuda") for _ in range(4))
+               for _ in range(2)]
         temp = torch.empty(binding.workspace_bytes("rs_sort_pairs_u32", n), dtype=torch.uint8,
                            device="cuda")
+        s_in, s_sort, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+        ev_in = [torch.cuda.Event() for _ in range(2)]
+        ev_sorted = [torch.cuda.Event() for _ in range(2)]
+        ev_out = [torch.cuda.Event() for _ in range(2)]
 
-        def e2e_step():
-            dk.copy_(hk, non_blocking=True)
-            dv.copy_(hv, non_blocking=True)
-            binding.rs_sort_pairs(dk, dv, ko, vo, ctx=ctx, temp=temp)
-            ok_h.copy_(ko, non_blocking=True)
-            ov_h.copy_(vo, non_blocking=True)
+        def run(steps):
+            for i in range(steps):
+                b = i & 1
+                dk, dv, ko, vo = dev[b]
+                with torch.cuda.stream(s_in):
+                    if i >= 2:
+                        s_in.wait_event(ev_sorted[b])  # the sort of step i-2 has read dk/dv
+                    dk.copy_(hk, non_blocking=True)
+                    dv.copy_(hv, non_blocking=True)
+                    ev_in[b].record(s_in)
+                with torch.cuda.stream(s_sort):
+                    s_sort.wait_event(ev_in[b])
+                    if i >= 2:
+                        s_sort.wait_event(ev_out[b])  # step i-2's results have left ko/vo
+                    binding.rs_sort_pairs(dk, dv, ko, vo, ctx=ctx, temp=temp, stream=s_sort)
+                    ev_sorted[b].record(s_sort)
+                with torch.cuda.stream(s_out):
+                    s_out.wait_event(ev_sorted[b])
+                    out_h[b][0].copy_(ko, non_blocking=True)
+                    out_h[b][1].copy_(vo, non_blocking=True)
+                    ev_out[b].record(s_out)
 
-        for _ in range(max(1, min(args.warmup, 3))):
-            e2e_step()
+        run(max(2, min(args.warmup, 3)))
         barrier()
+        steps = max(2, min(args.steps, 10))
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        steps = max(1, min(args.steps, 10))
-        e0.record(stream)
-        for _ in range(steps):
-            e2e_step()
-        e1.record(stream)
+        e0.record(s_in)
+        run(steps)
+        s_in.wait_stream(s_out)
+        e1.record(s_in)
         barrier()
         ctx.check()
-        ms_e2e = max_over_ranks(e0.elapsed_time(e1) / steps)
+        ms_e2e = max_over_ranks(e0.elapsed_time(e1) / steps, world)
+        got = out_h[(steps - 1) & 1][0][: 1 << 20].to(torch.int64) & 0xFFFFFFFF
+        assert bool((got[1:] >= got[:-1]).all()), "end-to-end output not sorted"
         e2e = {"value": world * n / (ms_e2e * 1e-3), "unit": "keys/s",
                "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n,
-               "ms_per_step": ms_e2e, "steps": steps}
-        del dk, dv, ko, vo, temp
+               "ms_per_step": ms_e2e, "steps": steps,
+               "pipeline": "3 streams, 2 buffer sets: H2D(i+1) | sort(i) | D2H(i-1)"}
+        del dev, temp
+        torch.cuda.empty_cache()
 
     seg = None
     if not args.no_segmented and world == 1:
@@ -460,15 +504,7 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "u32",
         "data": "synthetic",
-        "config": {
-            "workload": "2^28 u32 keys + u32 index payload (stable pairs sort), "
-                        f"{dists[0]} over [0,2^32)",
-            "n": n, "key": "u32", "value": "u32 index", "dist": dists[0],
-            "parallelism": f"replicas x{world}",
-            "l2": "inputs (2 GiB of keys+values) larger than the 129 MB L2; no flush",
-            "digit_bits": 8, "passes": head["passes_run"],
-            "alg_bytes_per_key": COUNT_BYTES_PER_KEY + PASS_BYTES_PER_KEY * head["passes_run"],
-        },
+        "config": workload_config(n, dists[0], world, head["passes_run"]),
         "hbm_gbs_alg": (COUNT_BYTES_PER_KEY + PASS_BYTES_PER_KEY * head["passes_run"]) * n
                        / (head["ms_per_step"] * 1e-3) / 1e9,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
