@@ -216,11 +216,12 @@ __device__ __forceinline__ uint32_t lanemask_gt() {
     return m;
 }
 
-// Exclusive scan of one value per thread over a 256-thread block.
-// s_warp must hold WARPS words; *total receives the block sum.
+// Exclusive scan of one value per thread over a block of NW warps.
+// s_warp must hold NW words; *total receives the block sum.
 // Contains __syncthreads(); every thread of the block must call it.
-__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* s_warp,
-                                                         uint32_t* total) {
+template <int NW>
+__device__ __forceinline__ uint32_t block_exclusive_scan_n(uint32_t v, uint32_t* s_warp,
+                                                           uint32_t* total) {
     const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
     uint32_t x = v;
 #pragma unroll
@@ -232,7 +233,7 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* s
     __syncthreads();
     uint32_t before = 0, sum = 0;
 #pragma unroll
-    for (int w = 0; w < WARPS; w++) {
+    for (int w = 0; w < NW; w++) {
         const uint32_t s = s_warp[w];
         before += (uint32_t)w < warp ? s : 0u;
         sum += s;
@@ -240,6 +241,12 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* s
     __syncthreads();  // s_warp may be reused by the caller
     *total = sum;
     return before + x - v;
+}
+
+// The same over the 256-thread blocks of the other kernels.
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* s_warp,
+                                                         uint32_t* total) {
+    return block_exclusive_scan_n<WARPS>(v, s_warp, total);
 }
 
 }  // namespace rs

@@ -289,9 +289,9 @@ struct ValTraits<NoVal> {
     static constexpr bool kPairs = false;
 };
 
-template <typename Cell, typename V, int IPT>
+template <typename Cell, typename V, int IPT, int PB = BLOCK>
 struct PassSmem {
-    static constexpr int TILE = BLOCK * IPT;
+    static constexpr int TILE = PB * IPT;
     static constexpr size_t kKeys = sizeof(Cell) * TILE;
     static constexpr size_t kVals = ValTraits<V>::kPairs ? sizeof(V) * TILE : 0;
     static constexpr size_t kBytes = kKeys + kVals;
@@ -307,64 +307,89 @@ __device__ __forceinline__ void* pick_dst(const PassArgs& a, uint32_t b, bool va
     return vals ? a.vals_out : a.keys_out;
 }
 
-// Decoupled look-back for one cell: the sum of this cell's counts over all
-// tiles before `tile`, walking back LOOKBACK_WINDOW predecessors per round
-// trip until a tile that already holds its inclusive prefix.  The wait for an unpublished
-// predecessor is bounded; on expiry the status word records a timeout and the
-// partial sum is returned so that every tile still finishes.
-__device__ __forceinline__ uint32_t lookback_prefix(const uint32_t* lookback, uint32_t tile,
-                                                    uint32_t cell, uint32_t* status,
-                                                    uint64_t timeout_ns = LOOKBACK_TIMEOUT_NS) {
-    uint32_t before = 0;
-    int64_t j = (int64_t)tile - 1;
+// Decoupled look-back for the ND cells a thread owns: for each, the sum of
+// its counts over all tiles before `tile`, walking back LOOKBACK_WINDOW
+// predecessor words per round trip (the ND walks overlap) until a tile that
+// already holds its inclusive prefix.  The wait for an unpublished
+// predecessor is bounded by time and by polls; on expiry the status word
+// records a timeout and the partial sums are returned so that every tile
+// still finishes.
+template <int ND>
+__device__ __forceinline__ void lookback_cells(const uint32_t* lookback, uint32_t tile,
+                                               const uint32_t (&cell)[ND], uint32_t* status,
+                                               uint32_t (&before)[ND],
+                                               uint64_t timeout_ns = LOOKBACK_TIMEOUT_NS) {
+    int64_t j[ND];
+    bool done[ND];
+#pragma unroll
+    for (int e = 0; e < ND; e++) {
+        before[e] = 0;
+        j[e] = (int64_t)tile - 1;
+        done[e] = j[e] < 0;
+    }
     const uint64_t t0 = global_ns();
     uint32_t spins = 0;
-    while (j >= 0) {
-        uint32_t s[LOOKBACK_WINDOW];
+    while (true) {
+        uint32_t sv[ND][LOOKBACK_WINDOW];
 #pragma unroll
-        for (int q = 0; q < LOOKBACK_WINDOW; q++)
-            s[q] = j - q >= 0 ? ld_relaxed(&lookback[(uint64_t)(j - q) * RADIX + cell])
-                              : LB_INCLUSIVE;
-        int consumed = 0;
-        bool done = false, blocked = false;
+        for (int e = 0; e < ND; e++)
 #pragma unroll
-        for (int q = 0; q < LOOKBACK_WINDOW; q++) {
-            if (done || blocked) continue;
-            const uint32_t flag = s[q] & ~LB_VALUE;
-            if (flag == 0) {
-                blocked = true;
-                continue;
+            for (int q = 0; q < LOOKBACK_WINDOW; q++)
+                sv[e][q] = (!done[e] && j[e] - q >= 0)
+                               ? ld_relaxed(&lookback[(uint64_t)(j[e] - q) * RADIX + cell[e]])
+                               : LB_INCLUSIVE;
+        bool progress = false, all_done = true;
+#pragma unroll
+        for (int e = 0; e < ND; e++) {
+            if (done[e]) continue;
+            int consumed = 0;
+            bool blocked = false;
+#pragma unroll
+            for (int q = 0; q < LOOKBACK_WINDOW; q++) {
+                if (done[e] || blocked) continue;
+                const uint32_t flag = sv[e][q] & ~LB_VALUE;
+                if (flag == 0) {
+                    blocked = true;
+                    continue;
+                }
+                before[e] += sv[e][q] & LB_VALUE;
+                consumed = q + 1;
+                done[e] = flag == LB_INCLUSIVE;
             }
-            before += s[q] & LB_VALUE;
-            consumed = q + 1;
-            done = flag == LB_INCLUSIVE;
+            j[e] -= consumed;
+            progress |= consumed > 0;
+            all_done &= done[e];
         }
-        if (done) break;
-        j -= consumed;
-        if (consumed == 0 && (++spins & 15u) == 0 &&
+        if (all_done) break;
+        if (!progress && (++spins & 15u) == 0 &&
             (global_ns() - t0 > timeout_ns || spins > LOOKBACK_MAX_POLLS)) {
             atomicOr(status, STATUS_TIMEOUT);
             break;  // give up; publish what we have so successors finish
         }
     }
-    return before;
 }
 
-template <class C, typename V, int IPT>
-__global__ void __launch_bounds__(BLOCK, sizeof(typename C::Cell) == 4 ? 3 : 2)
+// One digit-group pass over one tile of PB * IPT keys; PB threads per CTA,
+// each owning ND = 256 / PB consecutive cells in the per-cell phases.
+template <class C, typename V, int IPT, int PB>
+__global__ void __launch_bounds__(PB, PB == 256 ? (sizeof(typename C::Cell) == 4 ? 3 : 2)
+                                                 : (sizeof(typename C::Cell) == 4 ? 6 : 4))
     pass_kernel(PassArgs a) {
     using Cell = typename C::Cell;
     using In = typename C::In;
     using Out = typename C::Out;
     constexpr bool kPairs = ValTraits<V>::kPairs;
-    constexpr int TILE = BLOCK * IPT;
+    constexpr int TILE = PB * IPT;
+    constexpr int NW = PB / 32;
+    constexpr int ND = RADIX / PB;
+    static_assert(ND * PB == RADIX, "PB must divide the 256 cells");
     using VS = typename std::conditional<kPairs, V, uint32_t>::type;  // storage type
 
     // ws[w][d]: first the count of cell d in warp w's slice, then the
     // tile-local position where warp w's next key of cell d goes
-    __shared__ uint32_t ws[WARPS][RADIX];
+    __shared__ uint32_t ws[NW][RADIX];
     __shared__ uint32_t s_bin_global[RADIX];  // global position of tile-local index 0 per cell
-    __shared__ uint32_t s_warp[WARPS];
+    __shared__ uint32_t s_warp[NW];
     __shared__ uint32_t s_tile;
     extern __shared__ __align__(16) unsigned char smem_dyn[];
     Cell* s_keys = reinterpret_cast<Cell*>(smem_dyn);
@@ -372,17 +397,24 @@ __global__ void __launch_bounds__(BLOCK, sizeof(typename C::Cell) == 4 ? 3 : 2)
 
     const uint32_t t = threadIdx.x, lane = lane_id(), warp = t >> 5;
 
+    // The tile claim goes out first so its round trip overlaps the plan
+    // reads and the clearing below.  An inactive pass also claims: its
+    // counter is never read.
+    uint32_t claimed = 0;
+    if (t == 0) claimed = atomicAdd(a.tile_counter, 1u);
+
     // The next pass's look-back rows are free once this pass started: clear
     // one row per CTA (the grid has one CTA per tile).
-    a.lookback_next[(uint64_t)blockIdx.x * RADIX + t] = 0;
+#pragma unroll
+    for (int e = 0; e < ND; e++) a.lookback_next[(uint64_t)blockIdx.x * RADIX + e * PB + t] = 0;
+    for (uint32_t d = lane; d < RADIX; d += 32) ws[warp][d] = 0;
 
     const DevPlan* P = a.plan;
     if (P->mode != MODE_PASSES || !P->active[a.pass]) return;
     const bool first = P->first_active == a.pass;
     const bool last = P->last_active == a.pass;
 
-    if (t == 0) s_tile = atomicAdd(a.tile_counter, 1u);
-    for (uint32_t d = lane; d < RADIX; d += 32) ws[warp][d] = 0;
+    if (t == 0) s_tile = claimed;
     __syncthreads();
     const uint32_t tile = s_tile;
     const uint64_t tile_base = (uint64_t)tile * TILE;
@@ -432,21 +464,34 @@ __global__ void __launch_bounds__(BLOCK, sizeof(typename C::Cell) == 4 ? 3 : 2)
     __syncthreads();
 
     // ---- tile count per cell, publish it, then tile-local starts ----
-    uint32_t run = 0;
-#pragma unroll
-    for (int w = 0; w < WARPS; w++) {
-        const uint32_t x = ws[w][t];
-        ws[w][t] = run;
-        run += x;
-    }
-    // padding items carry cell ~0 (digit 255) and sit after every real item
-    const uint32_t count = t == RADIX - 1 ? run - (TILE - valid) : run;
+    uint32_t count[ND], excl[ND], cell[ND];
     uint32_t* lb = a.lookback + (uint64_t)tile * RADIX;
-    st_relaxed(&lb[t], (tile == 0 ? LB_INCLUSIVE : LB_AGGREGATE) | count);
-    uint32_t tile_total;
-    const uint32_t excl = block_exclusive_scan(count, s_warp, &tile_total);
+    uint32_t mine = 0;
 #pragma unroll
-    for (int w = 0; w < WARPS; w++) ws[w][t] += excl;
+    for (int e = 0; e < ND; e++) {
+        const uint32_t d = t * ND + e;
+        cell[e] = d;
+        uint32_t run = 0;
+#pragma unroll
+        for (int w = 0; w < NW; w++) {
+            const uint32_t x = ws[w][d];
+            ws[w][d] = run;
+            run += x;
+        }
+        // padding items carry cell ~0 (digit 255) and sit after every real item
+        count[e] = d == RADIX - 1 ? run - (TILE - valid) : run;
+        st_relaxed(&lb[d], (tile == 0 ? LB_INCLUSIVE : LB_AGGREGATE) | count[e]);
+        mine += count[e];
+    }
+    uint32_t tile_total;
+    uint32_t at = block_exclusive_scan_n<NW>(mine, s_warp, &tile_total);
+#pragma unroll
+    for (int e = 0; e < ND; e++) {
+        excl[e] = at;
+        at += count[e];
+#pragma unroll
+        for (int w = 0; w < NW; w++) ws[w][cell[e]] += excl[e];
+    }
     __syncthreads();
 
     // ---- stable rank in (cell, input) order, scattered into shared memory ----
@@ -456,49 +501,77 @@ __global__ void __launch_bounds__(BLOCK, sizeof(typename C::Cell) == 4 ? 3 : 2)
         const uint32_t d = digit_of(k[i], a.shift);
         const uint32_t peers = match_digit(d);
         uint32_t* slot = &ws[warp][d];
-        const uint32_t at = *slot;
+        const uint32_t pos0 = *slot;
         const uint32_t below = __popc(peers & lt);
         // every peer has read the slot before the highest one (the last of
         // them in input order) moves it past the group
         __syncwarp();
-        if ((peers & gt) == 0) *slot = at + below + 1;
-        const uint32_t pos = at + below;
+        if ((peers & gt) == 0) *slot = pos0 + below + 1;
+        const uint32_t pos = pos0 + below;
         s_keys[pos] = k[i];
         if constexpr (kPairs) s_vals[pos] = v[i];
         __syncwarp();
     }
 
-    // ---- decoupled look-back: this cell's count in all earlier tiles ----
+    // ---- decoupled look-back: these cells' counts in all earlier tiles ----
     // (after the ranking: the predecessors publish while this tile ranks)
-    uint32_t before = 0;
+    uint32_t before[ND];
     if (tile > 0) {
-        before = lookback_prefix(a.lookback, tile, t, a.status);
-        st_relaxed(&lb[t], LB_INCLUSIVE | ((before + count) & LB_VALUE));
+        lookback_cells<ND>(a.lookback, tile, cell, a.status, before);
+#pragma unroll
+        for (int e = 0; e < ND; e++)
+            st_relaxed(&lb[cell[e]], LB_INCLUSIVE | ((before[e] + count[e]) & LB_VALUE));
+    } else {
+#pragma unroll
+        for (int e = 0; e < ND; e++) before[e] = 0;
     }
-    s_bin_global[t] = a.bin_offsets[t] + before - excl;
+#pragma unroll
+    for (int e = 0; e < ND; e++)
+        s_bin_global[cell[e]] = a.bin_offsets[cell[e]] + before[e] - excl[e];
     __syncthreads();
 
     // ---- coalesced write-out: consecutive threads, consecutive positions ----
     void* kdst = pick_dst(a, P->dst[a.pass], false);
     VS* vdst = kPairs ? static_cast<VS*>(pick_dst(a, P->dst[a.pass], true)) : nullptr;
+    // (the clamp of g only acts after a timed-out wait: output unspecified)
+    const uint32_t gmax = (uint32_t)a.n - 1u;
     if (last) {
         Out* out = static_cast<Out*>(kdst);
-#pragma unroll 4
-        for (uint32_t j = t; j < valid; j += BLOCK) {
-            const Cell c = s_keys[j];
-            // the clamp only acts after a timed-out wait (output unspecified)
-            const uint32_t g = min(s_bin_global[digit_of(c, a.shift)] + j, (uint32_t)a.n - 1u);
-            __stcs(&out[g], C::encode(c, a.prm));
-            if constexpr (kPairs) __stcs(&vdst[g], s_vals[j]);
+        if (full) {
+#pragma unroll
+            for (int i = 0; i < IPT; i++) {
+                const uint32_t j = t + i * PB;
+                const Cell c = s_keys[j];
+                const uint32_t g = min(s_bin_global[digit_of(c, a.shift)] + j, gmax);
+                __stcs(&out[g], C::encode(c, a.prm));
+                if constexpr (kPairs) __stcs(&vdst[g], s_vals[j]);
+            }
+        } else {
+            for (uint32_t j = t; j < valid; j += PB) {
+                const Cell c = s_keys[j];
+                const uint32_t g = min(s_bin_global[digit_of(c, a.shift)] + j, gmax);
+                __stcs(&out[g], C::encode(c, a.prm));
+                if constexpr (kPairs) __stcs(&vdst[g], s_vals[j]);
+            }
         }
     } else {
         Cell* out = static_cast<Cell*>(kdst);
-#pragma unroll 4
-        for (uint32_t j = t; j < valid; j += BLOCK) {
-            const Cell c = s_keys[j];
-            const uint32_t g = min(s_bin_global[digit_of(c, a.shift)] + j, (uint32_t)a.n - 1u);
-            out[g] = c;
-            if constexpr (kPairs) vdst[g] = s_vals[j];
+        if (full) {
+#pragma unroll
+            for (int i = 0; i < IPT; i++) {
+                const uint32_t j = t + i * PB;
+                const Cell c = s_keys[j];
+                const uint32_t g = min(s_bin_global[digit_of(c, a.shift)] + j, gmax);
+                out[g] = c;
+                if constexpr (kPairs) vdst[g] = s_vals[j];
+            }
+        } else {
+            for (uint32_t j = t; j < valid; j += PB) {
+                const Cell c = s_keys[j];
+                const uint32_t g = min(s_bin_global[digit_of(c, a.shift)] + j, gmax);
+                out[g] = c;
+                if constexpr (kPairs) vdst[g] = s_vals[j];
+            }
         }
     }
 }
@@ -553,7 +626,9 @@ __global__ void __launch_bounds__(BLOCK) fill_kernel(FillArgs a) {
 static __global__ void __launch_bounds__(BLOCK) wait_timeout_kernel(const uint32_t* lookback,
                                                              uint32_t* status,
                                                              uint64_t timeout_ns) {
-    (void)lookback_prefix(lookback, 1, threadIdx.x, status, timeout_ns);
+    const uint32_t cell[1] = {threadIdx.x};
+    uint32_t before[1];
+    lookback_cells<1>(lookback, 1, cell, status, before, timeout_ns);
 }
 
 }  // namespace rs

@@ -68,7 +68,8 @@ extern "C" rs_status rs_sort_u32_noalloc(const uint32_t* keys_in, uint32_t* keys
 
     using C = CodecU32;
     constexpr int IPT = ipt_for<C, NoVal>();
-    constexpr int TILE = BLOCK * IPT;
+    constexpr int PB = pass_block<C, NoVal>();
+    constexpr int TILE = PB * IPT;
     constexpr uint32_t passes = 4;
     const Layout L = make_layout(n, passes, TILE, sizeof(uint32_t), 0);
     if (kHeader + L.total > RS_NOALLOC_SCRATCH_BYTES) return RS_ERR_TEMP_TOO_SMALL;
@@ -122,7 +123,7 @@ extern "C" rs_status rs_sort_u32_noalloc(const uint32_t* keys_in, uint32_t* keys
     const size_t per_cta = (size_t)BLOCK * FILL_IPT;
     fill_kernel<C><<<(unsigned)((n + per_cta - 1) / per_cta), BLOCK, 0, st>>>(f);
 
-    using Smem = PassSmem<uint32_t, NoVal, IPT>;
+    using Smem = PassSmem<uint32_t, NoVal, IPT, PB>;
     for (uint32_t p = 0; p < passes; p++) {
         PassArgs pa{};
         pa.keys_in = keys_in;
@@ -138,7 +139,7 @@ extern "C" rs_status rs_sort_u32_noalloc(const uint32_t* keys_in, uint32_t* keys
         pa.lookback_next = lb[(p + 1) & 1];
         pa.tile_counter = &plan->tile_counter[p];
         pa.status = status_word;
-        pass_kernel<C, NoVal, IPT><<<(unsigned)L.tiles, BLOCK, Smem::kBytes, st>>>(pa);
+        pass_kernel<C, NoVal, IPT, PB><<<(unsigned)L.tiles, PB, Smem::kBytes, st>>>(pa);
     }
     return cudaGetLastError() == cudaSuccess ? RS_OK : RS_ERR_CUDA;
 }

@@ -14,6 +14,10 @@
 #include "rs_ctx.hpp"
 #include "rs_kernels.cuh"
 
+#ifndef RS_PASS_BLOCK
+#define RS_PASS_BLOCK 256
+#endif
+
 namespace rs {
 
 inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
@@ -21,6 +25,12 @@ inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 // Keys per thread of a pass tile (256 threads).  For 32-bit cells 24 was
 // measured best on GB300 (12, 16, 20, 24, 28 tried; 3 CTAs per SM): larger
 // tiles amortise the per-tile scan, barriers and look-back.
+// Threads per CTA of the pass kernel.
+template <class C, typename V>
+constexpr int pass_block() {
+    return RS_PASS_BLOCK;
+}
+
 template <class C, typename V>
 constexpr int ipt_for() {
     return sizeof(typename C::Cell) == 4 ? (ValTraits<V>::kPairs && sizeof(V) > 4 ? 16 : 24) : 12;
@@ -91,7 +101,8 @@ rs_status run_sort(rs_ctx* ctx, const void* keys_in, void* keys_out, const void*
     using Cell = typename C::Cell;
     constexpr bool kPairs = ValTraits<V>::kPairs;
     constexpr int IPT = ipt_for<C, V>();
-    constexpr int TILE = BLOCK * IPT;
+    constexpr int PB = pass_block<C, V>();
+    constexpr int TILE = PB * IPT;
     const uint32_t passes = passes_for(cell_bits);
     const size_t vbytes = kPairs ? sizeof(V) : 0;
     const Layout L = make_layout(n, passes, TILE, sizeof(Cell), vbytes);
@@ -166,8 +177,8 @@ rs_status run_sort(rs_ctx* ctx, const void* keys_in, void* keys_out, const void*
         LaunchTimer lt(ctx, KC_FILL, stream);
         fill_kernel<C><<<grid, BLOCK, 0, stream>>>(f);
     }
-    using Smem = PassSmem<Cell, V, IPT>;
-    auto kern = pass_kernel<C, V, IPT>;
+    using Smem = PassSmem<Cell, V, IPT, PB>;
+    auto kern = pass_kernel<C, V, IPT, PB>;
     // static + dynamic shared memory may exceed the 48 KB default: opt in
     // once per device for this instantiation
     static bool smem_set[64] = {};
@@ -196,7 +207,7 @@ rs_status run_sort(rs_ctx* ctx, const void* keys_in, void* keys_out, const void*
         a.tile_counter = &plan->tile_counter[p];
         a.status = ctx->d_status;
         LaunchTimer lt(ctx, KC_PASS, stream);
-        kern<<<(unsigned)L.tiles, BLOCK, Smem::kBytes, stream>>>(a);
+        kern<<<(unsigned)L.tiles, PB, Smem::kBytes, stream>>>(a);
     }
     ctx->last_passes_total = passes;
     ctx->last_tiles = (uint32_t)L.tiles;
