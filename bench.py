@@ -32,7 +32,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "keys/s (2^28 u32) & HBM GB/s vs peak; batched vs per-call segmented keys/s"
 N_KEYS = 1 << 28
-ORACLE_SAMPLE = 1 << 24        # cpu_baseline: oracle on the first 2^24 pairs (~6-10 s)
+ORACLE_SAMPLE = 1 << 26        # cpu_baseline: oracle on the first 2^26 pairs (~12 s on Grace)
 REFERENCE_STEP_SAMPLE = 1 << 22
 PASS_BYTES_PER_KEY = 16        # one digit-group pass moves key+value in and out: 4+4+4+4
 COUNT_BYTES_PER_KEY = 4        # the counting pass reads each key once
@@ -509,7 +509,7 @@ def run_ours(args):
                        / (head["ms_per_step"] * 1e-3) / 1e9,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": traffic,
-                     "kernel": "pass_kernel<CodecU32,u32,16>",
+                     "kernel": "pass_kernel<CodecU32,u32,24>",
                      "alg_bytes_per_launch": PASS_BYTES_PER_KEY * n,
                      "launch_ms_avg": pass_ms, "peak_kind": f"{peak_kind} hbm_gbs"},
         "clocks": head["clocks"],
