@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--log2n", type=int, default=28)
     ap.add_argument("--no-segmented", action="store_true")
     ap.add_argument("--no-autograd", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the 10x10x10, decimal and string workloads")
     return ap.parse_args()
 
 
@@ -273,6 +275,119 @@ def segmented_leg(binding, ctx, steps: int, warmup: int):
             "speedup": per_call_ms / batched_ms}
 
 
+def configs_leg(binding, ctx, steps: int, warmup: int, hbm_peak: float):
+    """The other synthetic workloads, each timed with CUDA events on the
+    launching stream (inputs resident in HBM, outputs and workspace
+    preallocated):
+
+    * 2^20 u32 keys uniform in [0, 999] (one 10x10x10 count array, keys
+      only): cold (a 512 MB L2 flush before each sort), warm (back to back)
+      and replayed from a captured CUDA graph;
+    * 2^26 int64 fixed-point decimals, 6 + 3 digits, signed (keys only);
+    * 2^24 lowercase strings of 1..16 bytes (stable permutation).
+    """
+    import torch
+    from paper_2107_01391_gb300 import workloads as W
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn, reps, flush=None):
+        total = 0.0
+        for _ in range(reps):
+            if flush is not None:
+                flush()
+            ev[0].record(stream)
+            fn()
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            total += ev[0].elapsed_time(ev[1])
+        return total / reps
+
+    out = {}
+    # ---- 2^20 keys in a 10x10x10 space ----
+    n1 = 1 << 20
+    k1 = torch.from_numpy(W.digits3(n1).view(np.int32)).cuda()
+    o1 = torch.empty_like(k1)
+    t1 = torch.empty(binding.workspace_bytes("rs_sort_u32", n1), dtype=torch.uint8, device="cuda")
+    f1 = lambda: binding.rs_sort_u32(k1, o1, ctx=ctx, temp=t1)  # noqa: E731
+    for _ in range(warmup):
+        f1()
+    ctx.check()
+    plan1 = ctx.last_plan()
+    flush_buf = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    cold = timed(f1, steps, flush=lambda: flush_buf.fill_(1))
+    warm = timed(f1, steps)
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        f1()  # warm the side stream before capture
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g):
+        f1()
+    g.replay()
+    torch.cuda.synchronize()
+    graph_us = timed(g.replay, steps) * 1e3
+    ok1 = bool(torch.equal(o1.view(torch.int32), torch.sort(k1).values))
+    ctx.check()
+    del flush_buf, g
+    out["digits3_2p20"] = {
+        "workload": "2^20 u32 keys uniform in [0, 999], keys only (10x10x10 cells)",
+        "plan": plan1["mode"], "alg_bytes_per_key": 8,
+        "cold_us": cold * 1e3, "warm_us": warm * 1e3, "graph_us": graph_us,
+        "keys_per_s_warm": n1 / (warm * 1e-3), "keys_per_s_graph": n1 / (graph_us * 1e-6),
+        "matches_torch_sort": ok1,
+        "note": "L2-resident and launch-bound: no roofline claim"}
+
+    # ---- 2^26 signed fixed-point decimals ----
+    n3 = 1 << 26
+    k3 = torch.from_numpy(W.decimals(n3, 6, 3)).cuda()
+    o3 = torch.empty_like(k3)
+    t3 = torch.empty(binding.workspace_bytes("rs_sort_fixed_decimal", n3, int_digits=6,
+                                             frac_digits=3), dtype=torch.uint8, device="cuda")
+    f3 = lambda: binding.rs_sort_fixed_decimal(k3, 6, 3, o3, ctx=ctx, temp=t3)  # noqa: E731
+    for _ in range(warmup):
+        f3()
+    ctx.check()
+    plan3 = ctx.last_plan()
+    ms3 = timed(f3, steps)
+    ok3 = bool(torch.equal(o3, torch.sort(k3).values))
+    ctx.check()
+    # count reads int64 (8); the first pass reads int64 and writes u32 cells
+    # (12), middle passes 8, the last reads cells and writes int64 (12)
+    p3 = plan3["passes_run"]
+    b3 = 8 + (16 if p3 == 1 else 24 + 8 * (p3 - 2))
+    out["decimal_2p26"] = {
+        "workload": "2^26 int64 decimals, 6 integer + 3 fraction digits, signed, keys only",
+        "passes_run": p3, "alg_bytes_per_key": b3, "ms": ms3,
+        "keys_per_s": n3 / (ms3 * 1e-3), "alg_gbs": b3 * n3 / (ms3 * 1e-3) / 1e9,
+        "frac_of_measured_hbm": b3 * n3 / (ms3 * 1e-3) / 1e9 / hbm_peak,
+        "matches_torch_sort": ok3}
+    del k3, o3, t3
+
+    # ---- 2^24 strings ----
+    n4 = 1 << 24
+    chars, offs = W.strings(n4)
+    dc = torch.from_numpy(chars).cuda()
+    do = torch.from_numpy(offs.view(np.int32)).cuda()
+    po = torch.empty(n4, dtype=torch.int32, device="cuda")
+    t4 = None
+    for _ in range(warmup):
+        binding.rs_sort_strings(dc, do, 16, po, ctx=ctx, temp=t4)
+    ctx.check()
+    need = binding.workspace_bytes("rs_sort_strings", n4, max_len=16)
+    t4 = torch.empty(need, dtype=torch.uint8, device="cuda")
+    ms4 = timed(lambda: binding.rs_sort_strings(dc, do, 16, po, ctx=ctx, temp=t4), steps)
+    ctx.check()
+    out["strings_2p24"] = {
+        "workload": "2^24 lowercase strings, lengths uniform in 1..16 (stable permutation)",
+        "chars_bytes": int(chars.size), "ms": ms4, "keys_per_s": n4 / (ms4 * 1e-3)}
+    del dc, do, po, t4
+    torch.cuda.empty_cache()
+    return out
+
+
 def autograd_leg(steps: int, warmup: int):
     """Differentiable row sort: 4096 x 8192 float32 rows of distinct keys,
     forward (sorted values + stable permutation) and backward (gradient
@@ -483,6 +598,11 @@ def run_ours(args):
     if not args.no_autograd and world == 1:
         agl = autograd_leg(max(1, min(args.steps, 10)), max(1, min(args.warmup, 3)))
 
+    cfgs = None
+    if not args.no_configs and world == 1:
+        cfgs = configs_leg(binding, ctx, max(3, min(args.steps, 10)), max(3, min(args.warmup, 3)),
+                           hbm_peak)
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -520,6 +640,7 @@ def run_ours(args):
         "e2e": e2e,
         "segmented": seg,
         "autograd": agl,
+        "configs": cfgs,
         "cpu_baseline": (cpu_baseline(ORACLE_SAMPLE)
                          if world == 1 and not args.no_cpu_baseline else None),
     }

@@ -82,6 +82,8 @@ def lib() -> ctypes.CDLL:
         L.rs_sort_fixed_decimal.argtypes = [p, p, p, sz, ctypes.c_int, ctypes.c_int, p, psz, p]
         L.rs_sort_pairs.argtypes = [p, ctypes.c_int, p, p, p, p, sz, sz,
                                     ctypes.POINTER(KeyParams), p, psz, p]
+        L.rs_sort_strings.argtypes = [p, p, p, sz, ctypes.c_uint32, p, p, psz, p]
+        L.rs_sort_strings.restype = st
         for name in ("rs_ctx_create", "rs_ctx_destroy", "rs_ctx_status", "rs_ctx_last_plan",
                      "rs_ctx_set_timing", "rs_ctx_reset_timing", "rs_ctx_kernel_time",
                      "rs_sort_u32", "rs_sort_u64", "rs_sort_fixed_decimal", "rs_sort_pairs"):
@@ -291,6 +293,12 @@ def workspace_bytes(fn_name: str, n: int, **kw) -> int:
         code = L.rs_sort_u32(h, z, z, n, None, ctypes.byref(need), None)
     elif fn_name == "rs_sort_u64":
         code = L.rs_sort_u64(h, z, z, n, None, ctypes.byref(need), None)
+    elif fn_name == "rs_sort_fixed_decimal":
+        code = L.rs_sort_fixed_decimal(h, z, z, n, kw["int_digits"], kw["frac_digits"], None,
+                                       ctypes.byref(need), None)
+    elif fn_name == "rs_sort_strings":
+        code = L.rs_sort_strings(h, z, z, n, kw.get("max_len", RS_MAX_STRING_LEN), z, None,
+                                 ctypes.byref(need), None)
     elif fn_name == "rs_sort_pairs_u32":
         code = L.rs_sort_pairs(h, RS_KEY_U32, z, z, z, z, kw.get("val_bytes", 4), n, None, None,
                                ctypes.byref(need), None)
@@ -322,10 +330,6 @@ def rs_sort_strings(chars: torch.Tensor, offsets: torch.Tensor, max_len: int,
     ctx = ctx or default_context(offsets.device.index)
     L = lib()
     fn = L.rs_sort_strings
-    fn.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
-                   ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
-                   ctypes.POINTER(ctypes.c_size_t), ctypes.c_void_p]
-    fn.restype = ctypes.c_int
     s = _stream(offsets, stream)
     cptr = ctypes.c_void_p(chars.data_ptr()) if chars.numel() else ctypes.c_void_p(
         offsets.data_ptr())  # any valid device address; no byte is read when empty
