@@ -289,6 +289,26 @@ struct ValTraits<NoVal> {
     static constexpr bool kPairs = false;
 };
 
+// Tile shape of the pass kernel per (cell, value) type with 256-thread CTAs:
+// keys per thread (kIPT) and the resident CTAs per SM that its register
+// budget is compiled for (kCTAs).  Larger tiles amortise the per-tile scans
+// and look-back over more keys, so every shape takes the largest tile that
+// measured faster on GB300 (2^27-2^28 uniform keys):
+//   32-bit cells: keys only 48 (3 CTAs/SM; 64 and 80 at 2 CTAs/SM slower),
+//                 4-byte values 40 (2 CTAs/SM; 24 at 3 CTAs/SM, 32, 36, 44,
+//                 48 slower), 8-byte values 28;
+//   64-bit cells: keys only 40, 4-byte values 28, 8-byte values 24 (two
+//                 staging tiles of 96 KB fill the SM's shared memory).
+template <class C, typename V>
+struct PassShape {
+    static constexpr bool kPairs = ValTraits<V>::kPairs;
+    static constexpr bool kCell4 = sizeof(typename C::Cell) == 4;
+    static constexpr bool kVal8 = kPairs && sizeof(V) == 8;
+    static constexpr int kIPT = kCell4 ? (!kPairs ? 48 : (kVal8 ? 28 : 40))
+                                       : (!kPairs ? 40 : (kVal8 ? 24 : 28));
+    static constexpr int kCTAs = (kCell4 && !kPairs) ? 3 : 2;
+};
+
 template <typename Cell, typename V, int IPT, int PB = BLOCK>
 struct PassSmem {
     static constexpr int TILE = PB * IPT;
@@ -372,7 +392,7 @@ __device__ __forceinline__ void lookback_cells(const uint32_t* lookback, uint32_
 // One digit-group pass over one tile of PB * IPT keys; PB threads per CTA,
 // each owning ND = 256 / PB consecutive cells in the per-cell phases.
 template <class C, typename V, int IPT, int PB>
-__global__ void __launch_bounds__(PB, PB == 256 ? (sizeof(typename C::Cell) == 4 ? 3 : 2)
+__global__ void __launch_bounds__(PB, PB == 256 ? PassShape<C, V>::kCTAs
                                                  : (sizeof(typename C::Cell) == 4 ? 6 : 4))
     pass_kernel(PassArgs a) {
     using Cell = typename C::Cell;

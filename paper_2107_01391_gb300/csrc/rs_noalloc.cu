@@ -124,6 +124,12 @@ extern "C" rs_status rs_sort_u32_noalloc(const uint32_t* keys_in, uint32_t* keys
     fill_kernel<C><<<(unsigned)((n + per_cta - 1) / per_cta), BLOCK, 0, st>>>(f);
 
     using Smem = PassSmem<uint32_t, NoVal, IPT, PB>;
+    // this file's copy of the pass kernel needs its own opt-in to more than
+    // 48 KB of shared memory (static + dynamic)
+    if (cudaFuncSetAttribute(pass_kernel<C, NoVal, IPT, PB>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Smem::kBytes) != cudaSuccess)
+        return RS_ERR_CUDA;
     for (uint32_t p = 0; p < passes; p++) {
         PassArgs pa{};
         pa.keys_in = keys_in;

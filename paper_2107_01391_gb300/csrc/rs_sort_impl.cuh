@@ -22,18 +22,16 @@ namespace rs {
 
 inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 
-// Keys per thread of a pass tile (256 threads).  For 32-bit cells 24 was
-// measured best on GB300 (12, 16, 20, 24, 28 tried; 3 CTAs per SM): larger
-// tiles amortise the per-tile scan, barriers and look-back.
 // Threads per CTA of the pass kernel.
 template <class C, typename V>
 constexpr int pass_block() {
     return RS_PASS_BLOCK;
 }
 
+// Keys per thread of a pass tile (PassShape).
 template <class C, typename V>
 constexpr int ipt_for() {
-    return sizeof(typename C::Cell) == 4 ? (ValTraits<V>::kPairs && sizeof(V) > 4 ? 16 : 24) : 12;
+    return PassShape<C, V>::kIPT;
 }
 
 struct Layout {

@@ -1,7 +1,7 @@
 """Parity of the CUDA path against the CPU oracle, element by element.
 
-Sizes span several tiles (6144 keys for 32-bit cells, 3072 for 64-bit) with
-ragged tails; every comparison is bit-exact (keys, and payload order for
+Sizes span several tiles (see TILE_KEYS: 256 threads times the keys per
+thread of each key/value shape) with ragged tails; every comparison is bit-exact (keys, and payload order for
 pairs).  All calls go through the C ABI via the thin binding.
 """
 import numpy as np
@@ -13,8 +13,12 @@ from paper_2107_01391_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-# pass tiles hold 6144 keys (32-bit cells) or 3072 (64-bit cells)
-SIZES_U32 = [1, 2, 3, 31, 4095, 4097, 6143, 6144, 6145, 3 * 6144 + 17, 100_003]
+# keys per pass tile (256 threads x keys per thread) for each (key, value) shape;
+# test_tile_boundaries checks these against the tile count the library reports
+TILE_KEYS = {("u32", None): 48 * 256, ("u32", "u32"): 40 * 256, ("u32", "u64"): 28 * 256,
+             ("u64", None): 40 * 256, ("u64", "u32"): 28 * 256, ("u64", "u64"): 24 * 256}
+_T32 = TILE_KEYS[("u32", None)]
+SIZES_U32 = [1, 2, 3, 31, 4095, 4097, _T32 - 1, _T32, _T32 + 1, 3 * _T32 + 17, 100_003]
 
 
 @pytest.fixture(scope="module")
@@ -103,7 +107,7 @@ def test_empty(rs, ctx):
     assert out.numel() == 0
 
 
-@pytest.mark.parametrize("n", [1, 3071, 3072, 3073, 70_001])
+@pytest.mark.parametrize("n", [1, 3071, 3072, 3073, 10_239, 10_241, 70_001])
 def test_u64_keys(rs, ctx, oracle, n):
     keys = W.u64_keys(n, seed_extra=n)
     ref, _, _ = oracle.sort_u64(keys)
@@ -111,6 +115,31 @@ def test_u64_keys(rs, ctx, oracle, n):
     out = rs.rs_sort_u64(d, ctx=ctx)
     ctx.check()
     assert np.array_equal(from_dev(out, np.uint64), ref)
+
+
+@pytest.mark.parametrize("where", ["minus1", "exact", "plus1", "ragged3"])
+@pytest.mark.parametrize("shape", list(TILE_KEYS), ids=lambda s: f"{s[0]}-{s[1]}")
+def test_tile_boundaries(rs, ctx, oracle, shape, where):
+    kt, vt = shape
+    T = TILE_KEYS[shape]
+    n = {"minus1": T - 1, "exact": T, "plus1": T + 1, "ragged3": 3 * T + 17}[where]
+    kdt = np.uint32 if kt == "u32" else np.uint64
+    keys = (W.u32_keys(n, seed_extra=n) if kt == "u32" else W.u64_keys(n, seed_extra=n))
+    keys[1::5] = keys[0::5][: keys[1::5].size]  # ties, so that stability is checked
+    if vt is None:
+        ref, _, _ = oracle.sort_u32(keys) if kt == "u32" else oracle.sort_u64(keys)
+        out = (rs.rs_sort_u32 if kt == "u32" else rs.rs_sort_u64)(to_dev(keys), ctx=ctx)
+        ctx.check()
+        assert np.array_equal(from_dev(out, kdt), ref)
+    else:
+        vdt = np.uint32 if vt == "u32" else np.uint64
+        vals = (np.arange(n, dtype=vdt) * vdt(2654435761)) ^ vdt(0x5A5A5A5A)
+        ref_k, ref_v, _ = oracle.sort_pairs(keys, vals)
+        ko, vo = rs.rs_sort_pairs(to_dev(keys), to_dev(vals), ctx=ctx)
+        ctx.check()
+        assert np.array_equal(from_dev(ko, kdt), ref_k)
+        assert np.array_equal(from_dev(vo, vdt), ref_v)
+    assert ctx.last_plan()["tiles"] == -(-n // T)
 
 
 # --------------------------------------------------------------- decimals
