@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--log2n", type=int, default=28)
     ap.add_argument("--no-segmented", action="store_true")
     ap.add_argument("--no-autograd", action="store_true")
+    ap.add_argument("--no-run-a", action="store_true",
+                    help="skip the 6.2e9-key segmented run (148 GB of device memory)")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the 10x10x10, decimal and string workloads")
     return ap.parse_args()
@@ -198,55 +200,22 @@ def cpu_baseline(sample_n: int):
                       f"u32-pairs workload, one oracle call, {dt:.2f} s single-threaded"}
 
 
-def segmented_leg(binding, ctx, steps: int, warmup: int):
-    """Batched segmented sort against one call per segment, same GPU, same data.
-
-    Workload: 65536 segments with log-uniform sizes in [16, 2^20], rescaled so
-    they sum to 2^28 keys (u32 keys, f32 values).  Both forms go through the
-    C ABI; the per-call form issues one rs_sort_pairs per segment on the same
-    stream with preallocated outputs and workspace.
-    """
+def _per_call_pairs(binding, ctx, dk, dv, ko, vo, starts, lens, stream):
+    """One rs_sort_pairs call per segment through the raw C ABI, on the same
+    stream, with preallocated outputs and a workspace for the largest one."""
     import ctypes
     import torch
-    from paper_2107_01391_gb300 import workloads as W
-    sizes = W.segment_sizes(65536, total=1 << 28)
-    keys, vals, off = W.segments(sizes)
-    n = keys.size
-    dk = torch.from_numpy(keys.view(np.int32)).cuda()
-    dv = torch.from_numpy(vals).cuda()
-    doff = torch.from_numpy(off.view(np.int64)).cuda()
-    ko, vo = torch.empty_like(dk), torch.empty_like(dv)
-    stream = torch.cuda.current_stream()
-    temp = None
-    for _ in range(warmup):
-        _, _ = binding.rs_sort_segmented(dk, doff, dv, ko, vo, ctx=ctx, temp=temp)
-    ctx.check()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    launches0 = ctx.launch_count()
-    e0.record(stream)
-    for _ in range(steps):
-        binding.rs_sort_segmented(dk, doff, dv, ko, vo, ctx=ctx)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ctx.check()
-    batched_ms = e0.elapsed_time(e1) / steps
-    seg_launches = (ctx.launch_count() - launches0) / steps
-
-    # one call per segment: raw C-ABI calls in a loop
     L = binding.lib()
-    big = int(sizes.max())
     need = ctypes.c_size_t(0)
     z = ctypes.c_void_p(256)
-    L.rs_sort_pairs(ctx.handle, binding.RS_KEY_U32, z, z, z, z, 4, big, None, None,
+    L.rs_sort_pairs(ctx.handle, binding.RS_KEY_U32, z, z, z, z, 4, max(lens), None, None,
                     ctypes.byref(need), None)
     tmp = torch.empty(need.value, dtype=torch.uint8, device="cuda")
     kb, vb, ob, pb = dk.data_ptr(), dv.data_ptr(), ko.data_ptr(), vo.data_ptr()
     sptr = ctypes.c_void_p(stream.cuda_stream)
     tptr = ctypes.c_void_p(tmp.data_ptr())
-    starts = off[:-1].astype(np.int64).tolist()
-    lens = sizes.astype(np.int64).tolist()
 
-    def per_call():
+    def run():
         for lo, ln in zip(starts, lens):
             tb = ctypes.c_size_t(need.value)
             rc = L.rs_sort_pairs(ctx.handle, 0, ctypes.c_void_p(kb + 4 * lo),
@@ -256,23 +225,114 @@ def segmented_leg(binding, ctx, steps: int, warmup: int):
             if rc:
                 raise RuntimeError(f"rs_sort_pairs failed: {rc}")
 
-    per_call()
+    run()
     torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    per_call()
+    run()
     e1.record(stream)
     torch.cuda.synchronize()
     ctx.check()
-    per_call_ms = e0.elapsed_time(e1)
-    del dk, dv, ko, vo, tmp
+    return e0.elapsed_time(e1)
+
+
+def _batched_segmented(binding, ctx, dk, dv, doff, ko, vo, steps, warmup, stream):
+    import torch
+    for _ in range(warmup):
+        binding.rs_sort_segmented(dk, doff, dv, ko, vo, ctx=ctx)
+    ctx.check()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = ctx.launch_count()
+    e0.record(stream)
+    for _ in range(steps):
+        binding.rs_sort_segmented(dk, doff, dv, ko, vo, ctx=ctx)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ctx.check()
+    return e0.elapsed_time(e1) / steps, (ctx.launch_count() - launches0) / steps
+
+
+def segmented_leg(binding, ctx, steps: int, warmup: int, run_a: bool = True):
+    """Batched segmented sort against one call per segment, same GPU, same data.
+
+    Both runs draw 65536 segment sizes log-uniform in [16, 2^20] (u32 keys,
+    f32 values).  Run B rescales them to sum to 2^28 keys (its keys come from
+    the seeded host generator); Run A keeps the draws as printed, about
+    6.2e9 keys in total, whose keys and values are drawn on the device (torch
+    Philox, seeded) since the host would need minutes for them.  Both forms
+    go through the C ABI; the per-call form issues one rs_sort_pairs per
+    segment on the same stream with preallocated outputs and workspace.
+    """
+    import torch
+    from paper_2107_01391_gb300 import workloads as W
+    stream = torch.cuda.current_stream()
+
+    # ---- Run B: 2^28 keys ----
+    sizes = W.segment_sizes(65536, total=1 << 28)
+    keys, vals, off = W.segments(sizes)
+    n = keys.size
+    dk = torch.from_numpy(keys.view(np.int32)).cuda()
+    dv = torch.from_numpy(vals).cuda()
+    doff = torch.from_numpy(off.view(np.int64)).cuda()
+    ko, vo = torch.empty_like(dk), torch.empty_like(dv)
+    batched_ms, seg_launches = _batched_segmented(binding, ctx, dk, dv, doff, ko, vo, steps,
+                                                  warmup, stream)
+    per_call_ms = _per_call_pairs(binding, ctx, dk, dv, ko, vo, off[:-1].astype(np.int64).tolist(),
+                                  sizes.astype(np.int64).tolist(), stream)
+    out = {"workload": "65536 segments, log-uniform sizes 16..2^20 rescaled to sum 2^28 "
+                       "(Run B), u32 keys + f32 values",
+           "total_keys": int(n), "num_segs": int(sizes.size), "max_seg": int(sizes.max()),
+           "batched_ms": batched_ms, "batched_keys_per_s": n / (batched_ms * 1e-3),
+           "batched_launches": seg_launches,
+           "per_call_ms": per_call_ms, "per_call_keys_per_s": n / (per_call_ms * 1e-3),
+           "speedup": per_call_ms / batched_ms}
+    del dk, dv, doff, ko, vo
     torch.cuda.empty_cache()
-    return {"workload": "65536 segments, log-uniform sizes 16..2^20 rescaled to sum 2^28 "
-                        "(Run B), u32 keys + f32 values",
-            "total_keys": int(n), "num_segs": int(sizes.size), "max_seg": big,
-            "batched_ms": batched_ms, "batched_keys_per_s": n / (batched_ms * 1e-3),
-            "batched_launches": seg_launches,
-            "per_call_ms": per_call_ms, "per_call_keys_per_s": n / (per_call_ms * 1e-3),
-            "speedup": per_call_ms / batched_ms}
+    if not run_a:
+        return out
+
+    # ---- Run A: the sizes as drawn ----
+    sizes = W.segment_sizes(65536)
+    off = np.zeros(sizes.size + 1, np.int64)
+    np.cumsum(sizes, out=off[1:])
+    n = int(off[-1])
+    need = n * 24 + (1 << 30)  # keys, values, outputs, workspace
+    free = torch.cuda.mem_get_info()[0]
+    if need > free:
+        out["run_a"] = {"skipped": f"needs {need / 1e9:.0f} GB, {free / 1e9:.0f} GB free"}
+        return out
+    g = torch.Generator(device="cuda")
+    g.manual_seed(W.SEED_BASE + W.WORKLOAD_IDS["segments"] + 200)
+    dk = torch.empty(n, dtype=torch.int32, device="cuda")
+    dv = torch.empty(n, dtype=torch.float32, device="cuda")
+    chunk = 1 << 28
+    for lo in range(0, n, chunk):
+        hi = min(n, lo + chunk)
+        dk[lo:hi] = torch.randint(0, 1 << 32, (hi - lo,), dtype=torch.int64, device="cuda",
+                                  generator=g).to(torch.int32)
+        dv[lo:hi] = torch.randn(hi - lo, dtype=torch.float32, device="cuda", generator=g)
+    doff = torch.from_numpy(off).cuda()
+    ko, vo = torch.empty_like(dk), torch.empty_like(dv)
+    a_steps = max(1, min(steps, 3))
+    batched_ms, seg_launches = _batched_segmented(binding, ctx, dk, dv, doff, ko, vo, a_steps,
+                                                  1, stream)
+    # spot check: the largest and the smallest segment come out sorted
+    for s in (int(np.argmax(sizes)), int(np.argmin(sizes))):
+        seg = ko[int(off[s]):int(off[s + 1])].to(torch.int64) & 0xFFFFFFFF
+        assert bool((seg[1:] >= seg[:-1]).all()), "Run A segment not sorted"
+    per_call_ms = _per_call_pairs(binding, ctx, dk, dv, ko, vo, off[:-1].tolist(),
+                                  sizes.astype(np.int64).tolist(), stream)
+    out["run_a"] = {
+        "workload": "65536 segments, log-uniform sizes 16..2^20 as drawn (Run A), u32 keys "
+                    "+ f32 values drawn on the device",
+        "total_keys": n, "max_seg": int(sizes.max()),
+        "batched_ms": batched_ms, "batched_keys_per_s": n / (batched_ms * 1e-3),
+        "batched_launches": seg_launches,
+        "per_call_ms": per_call_ms, "per_call_keys_per_s": n / (per_call_ms * 1e-3),
+        "speedup": per_call_ms / batched_ms}
+    del dk, dv, doff, ko, vo
+    torch.cuda.empty_cache()
+    return out
 
 
 def configs_leg(binding, ctx, steps: int, warmup: int, hbm_peak: float):
@@ -605,7 +665,8 @@ def run_ours(args):
 
     seg = None
     if not args.no_segmented and world == 1:
-        seg = segmented_leg(binding, ctx, max(1, min(args.steps, 10)), max(1, min(args.warmup, 3)))
+        seg = segmented_leg(binding, ctx, max(1, min(args.steps, 10)), max(1, min(args.warmup, 3)),
+                            run_a=not args.no_run_a)
 
     agl = None
     if not args.no_autograd and world == 1:

@@ -164,10 +164,14 @@ rs_status rs_sort_strings(rs_ctx* ctx, const uint8_t* chars, const uint32_t* off
  *               receives, for every output position, the index within its
  *               segment of the key placed there (an argsort), as val_bytes
  *               (4 or 8) unsigned integers.
- * Offsets that decrease or pass n raise RS_ERR_RANGE (device-detected) and
- * the offending segment is skipped.  One launch sorts every segment: segments
- * of at most 4096 keys are sorted on chip in one read and one write; larger
- * ones by one CTA each, largest first. */
+ * n may exceed RS_MAX_N, up to RS_MAX_SEGMENTED_N; a single segment holds at
+ * most RS_MAX_SEGMENT_LEN keys.  Offsets that decrease or pass n, or a longer
+ * segment, raise RS_ERR_RANGE (device-detected) and the offending segment is
+ * skipped.  One launch sorts every segment, largest first: segments of at
+ * most 63 keys by one warp each, of at most 4096 keys on chip by one CTA in
+ * one read and one write, larger ones by one CTA each. */
+#define RS_MAX_SEGMENTED_N (1ull << 40)
+#define RS_MAX_SEGMENT_LEN 0xffffffffull
 rs_status rs_sort_segmented(rs_ctx* ctx, rs_key_type kt, const void* keys_in, void* keys_out,
                             const void* vals_in, void* vals_out, size_t val_bytes, size_t n,
                             const uint64_t* seg_offsets, size_t num_segs,

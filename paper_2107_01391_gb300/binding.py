@@ -27,6 +27,8 @@ STATUS_NAMES = {0: "RS_OK", 1: "RS_ERR_INVALID", 2: "RS_ERR_RANGE", 3: "RS_ERR_T
                 4: "RS_ERR_CUDA", 5: "RS_ERR_TIMEOUT", 6: "RS_ERR_UNSUPPORTED"}
 RS_KEY_U32, RS_KEY_U64, RS_KEY_I64_DEC, RS_KEY_F32, RS_KEY_F64 = 0, 1, 2, 3, 4
 RS_MAX_N = (1 << 30) - 1
+RS_MAX_SEGMENTED_N = 1 << 40
+RS_MAX_SEGMENT_LEN = (1 << 32) - 1
 RS_FILL_CELLS = 4096
 
 # Every function the header declares (the CPU test checks the export table).
@@ -83,7 +85,15 @@ def lib() -> ctypes.CDLL:
         L.rs_sort_pairs.argtypes = [p, ctypes.c_int, p, p, p, p, sz, sz,
                                     ctypes.POINTER(KeyParams), p, psz, p]
         L.rs_sort_strings.argtypes = [p, p, p, sz, ctypes.c_uint32, p, p, psz, p]
-        L.rs_sort_strings.restype = st
+        L.rs_sort_segmented.argtypes = [p, ctypes.c_int, p, p, p, p, sz, sz, p, sz,
+                                        ctypes.POINTER(KeyParams), p, psz, p]
+        L.rs_scatter_rows.argtypes = [p, p, p, sz, sz, sz, p, p]
+        L.rs_traverse_maps.argtypes = [p, p, sz, ctypes.c_int, ctypes.c_int, ctypes.c_int, p, p,
+                                       p, p, p, psz, p]
+        L.rs_sort_u32_noalloc.argtypes = [p, p, sz, p, p]
+        for name in ("rs_sort_strings", "rs_sort_segmented", "rs_scatter_rows",
+                     "rs_traverse_maps", "rs_sort_u32_noalloc"):
+            getattr(L, name).restype = st
         for name in ("rs_ctx_create", "rs_ctx_destroy", "rs_ctx_status", "rs_ctx_last_plan",
                      "rs_ctx_set_timing", "rs_ctx_reset_timing", "rs_ctx_kernel_time",
                      "rs_sort_u32", "rs_sort_u64", "rs_sort_fixed_decimal", "rs_sort_pairs"):
@@ -386,11 +396,6 @@ def rs_sort_segmented(keys: torch.Tensor, seg_offsets: torch.Tensor | None,
     ctx = ctx or default_context(keys.device.index)
     L = lib()
     fn = L.rs_sort_segmented
-    fn.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
-                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_size_t,
-                   ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(KeyParams), ctypes.c_void_p,
-                   ctypes.POINTER(ctypes.c_size_t), ctypes.c_void_p]
-    fn.restype = ctypes.c_int
     prm = KeyParams(*(decimal or (0, 0)))
     s = _stream(keys, stream)
     vin = _ptr(values) if values is not None else ctypes.c_void_p(0)
@@ -419,9 +424,6 @@ def rs_scatter_rows(src: torch.Tensor, perm: torch.Tensor, out: torch.Tensor | N
     ctx = ctx or default_context(src.device.index)
     L = lib()
     fn = L.rs_scatter_rows
-    fn.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
-                   ctypes.c_size_t, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p]
-    fn.restype = ctypes.c_int
     _check(fn(ctx.handle, _ptr(src), _ptr(perm), src.shape[0], src.shape[1],
               src.element_size(), _ptr(out), _stream(src, stream)), "rs_scatter_rows")
     return out
@@ -448,11 +450,6 @@ def rs_traverse_maps(keys: torch.Tensor, int_digits: int, frac_digits: int,
     ctx = ctx or default_context(dev.index)
     L = lib()
     fn = L.rs_traverse_maps
-    fn.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_int,
-                   ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-                   ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t),
-                   ctypes.c_void_p]
-    fn.restype = ctypes.c_int
     s = _stream(keys, stream)
     sp = _ptr(S) if S is not None else ctypes.c_void_p(0)
 
@@ -478,9 +475,6 @@ def rs_sort_u32_noalloc(keys: torch.Tensor, out: torch.Tensor | None = None,
     """
     L = lib()
     fn = L.rs_sort_u32_noalloc
-    fn.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
-                   ctypes.c_void_p]
-    fn.restype = ctypes.c_int
     _cuda(keys, "keys", 4, U32_DTYPES)
     out = torch.empty_like(keys) if out is None else _cuda(out, "out", 4, U32_DTYPES)
     st = _ptr(status) if status is not None else ctypes.c_void_p(0)

@@ -7,6 +7,10 @@
 //                        counting sort of the segments by size, largest first)
 //   2. seg_order_kernel  writes the segment ids in that order
 //   3. seg_sort_kernel   persistent CTAs take segments from the ordered list:
+//        - once the list reaches segments of at most 63 keys (everything
+//          after them is as small), a CTA takes eight at a time and each
+//          warp sorts one: two keys per lane, each ranked by counting the
+//          keys before it in (cell, position) order;
 //        - a segment of at most one tile is loaded once into registers and
 //          sorted entirely on chip: one rank-and-scatter through shared
 //          memory per 8-bit digit group, then one coalesced write
@@ -30,6 +34,8 @@ namespace {
 constexpr int SEG_IPT = 16;
 constexpr uint32_t SEG_TILE = BLOCK * SEG_IPT;
 constexpr int SIZE_CLASSES = 64;
+constexpr uint64_t WARP_SEG_MAX = 63;         // segments sorted by one warp
+constexpr uint64_t SEG_MAX_LEN = 0xffffffffull;  // counts within a segment are 32-bit
 
 struct SegControl {
     uint32_t class_count[SIZE_CLASSES];
@@ -68,11 +74,11 @@ __device__ __forceinline__ bool seg_bounds(const SegArgs& a, uint64_t s, uint64_
     if (!a.seg_offsets) {
         lo = s * a.seg_len;
         hi = lo + a.seg_len;
-        return true;
+        return a.seg_len <= SEG_MAX_LEN;
     }
     lo = a.seg_offsets[s];
     hi = a.seg_offsets[s + 1];
-    return lo <= hi && hi <= a.n;
+    return lo <= hi && hi <= a.n && hi - lo <= SEG_MAX_LEN;
 }
 
 __global__ void __launch_bounds__(BLOCK) seg_size_kernel(SegArgs a) {
@@ -144,12 +150,64 @@ __device__ __forceinline__ void load_tile(const void* ksrc, const VS* vsrc, uint
     if (!ok) atomicOr(status, STATUS_RANGE);
 }
 
+// One segment of at most WARP_SEG_MAX keys sorted by one warp: lane l holds
+// positions l and l + 32; a key's output position is the number of keys of
+// the segment before it in (cell, input position) order, which is its
+// stable rank.  Every input is in registers before the first store, so the
+// segment may be sorted in place.
+template <class C, typename VS, bool kPairs>
+__device__ __forceinline__ void warp_sort_segment(const SegArgs& a, uint32_t seg, uint32_t lane) {
+    using Cell = typename C::Cell;
+    using In = typename C::In;
+    using Out = typename C::Out;
+    uint64_t lo, hi;
+    if (!seg_bounds(a, seg, lo, hi) || hi == lo) return;  // bad bounds were flagged
+    const uint32_t len = (uint32_t)(hi - lo);
+    Cell c[2];
+    VS v[2];
+    bool ok = true;
+#pragma unroll
+    for (int e = 0; e < 2; e++) {
+        const uint32_t j = lane + 32 * e;
+        c[e] = ~Cell(0);
+        v[e] = VS(0);
+        if (j < len) {
+            c[e] = C::decode(static_cast<const In*>(a.keys_in)[lo + j], a.prm, ok);
+            if constexpr (kPairs)
+                v[e] = a.iota ? (VS)j : static_cast<const VS*>(a.vals_in)[lo + j];
+        }
+    }
+    if (!ok) atomicOr(a.status, STATUS_RANGE);
+    uint32_t r[2] = {0, 0};
+#pragma unroll
+    for (int e2 = 0; e2 < 2; e2++) {
+        for (uint32_t src = 0; src < 32; src++) {
+            const Cell o = __shfl_sync(0xffffffffu, c[e2], src);
+            const uint32_t po = src + 32 * e2;
+            if (po >= len) break;  // uniform across the warp
+#pragma unroll
+            for (int e = 0; e < 2; e++) {
+                const uint32_t pm = lane + 32 * e;
+                r[e] += (o < c[e] || (o == c[e] && po < pm)) ? 1u : 0u;
+            }
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int e = 0; e < 2; e++) {
+        if (lane + 32 * e < len) {
+            static_cast<Out*>(a.keys_out)[lo + r[e]] = C::encode(c[e], a.prm);
+            if constexpr (kPairs) static_cast<VS*>(a.vals_out)[lo + r[e]] = v[e];
+        }
+    }
+}
+
 // Resident CTAs per SM: three (80 registers a thread) measured 10% faster
-// than two on 2^28 keys in log-uniform segments; 8-byte keys with 8-byte
-// payloads keep two, since they spill at 80 registers.
+// than two on 2^28 u32 keys + 4-byte values in log-uniform segments; shapes
+// with an 8-byte cell or value keep two, since they spill at 80 registers.
 template <class C, typename V>
 constexpr int seg_ctas_per_sm() {
-    return (sizeof(typename C::Cell) == 8 && ValTraits<V>::kPairs && sizeof(V) == 8) ? 2 : 3;
+    return (sizeof(typename C::Cell) == 4 && (!ValTraits<V>::kPairs || sizeof(V) == 4)) ? 3 : 2;
 }
 
 template <class C, typename V>
@@ -163,7 +221,7 @@ __global__ void __launch_bounds__(BLOCK, seg_ctas_per_sm<C, V>()) seg_sort_kerne
     __shared__ TileShared ts;
     __shared__ uint32_t s_hist[MAX_PASSES][RADIX];  // whole-segment counts (large segments)
     __shared__ uint32_t s_run[RADIX];              // running cell offsets of the sweep
-    __shared__ uint32_t s_seg;
+    __shared__ uint32_t s_first, s_take;
     __shared__ uint32_t s_active[MAX_PASSES];
     extern __shared__ __align__(16) unsigned char smem_dyn[];
     Cell* s_keys = reinterpret_cast<Cell*>(smem_dyn);
@@ -172,13 +230,28 @@ __global__ void __launch_bounds__(BLOCK, seg_ctas_per_sm<C, V>()) seg_sort_kerne
 
     while (true) {
         if (t == 0) {
-            const uint32_t w = atomicAdd(&a.ctl->work, 1u);
-            s_seg = w < a.num_segs ? a.order[w] : 0xffffffffu;
+            // The list is ordered by size class, largest first: once the next
+            // entry is a warp-sized segment every later one is too, so take
+            // one per warp.
+            uint32_t take = 1;
+            const uint32_t peek = ld_relaxed(&a.ctl->work);
+            uint64_t plo, phi;
+            if (peek < a.num_segs && seg_bounds(a, a.order[peek], plo, phi) &&
+                phi - plo <= WARP_SEG_MAX)
+                take = WARPS;
+            s_first = atomicAdd(&a.ctl->work, take);
+            s_take = take;
         }
         __syncthreads();
-        const uint32_t seg = s_seg;
+        const uint32_t first_w = s_first, take = s_take;
         __syncthreads();
-        if (seg == 0xffffffffu) return;
+        if (first_w >= a.num_segs) return;
+        if (take > 1) {
+            if (first_w + warp < a.num_segs)
+                warp_sort_segment<C, VS, kPairs>(a, a.order[first_w + warp], lane);
+            continue;
+        }
+        const uint32_t seg = a.order[first_w];
         uint64_t lo, hi;
         if (!seg_bounds(a, seg, lo, hi) || hi == lo) continue;
         const uint64_t len = hi - lo;
@@ -417,7 +490,7 @@ extern "C" rs_status rs_sort_segmented(rs_ctx* ctx, rs_key_type kt, const void* 
                                        size_t num_segs, const rs_key_params* params, void* temp,
                                        size_t* temp_bytes, rs_stream_t stream) {
     if (!ctx || !temp_bytes) return RS_ERR_INVALID;
-    if (n > RS_MAX_N || num_segs > 0xfffffffeull) return RS_ERR_INVALID;
+    if (n > RS_MAX_SEGMENTED_N || num_segs > 0xfffffffeull) return RS_ERR_INVALID;
     if (kt != RS_KEY_U32 && kt != RS_KEY_U64 && kt != RS_KEY_I64_DEC && kt != RS_KEY_F32 &&
         kt != RS_KEY_F64)
         return RS_ERR_UNSUPPORTED;

@@ -96,6 +96,20 @@ def test_argument_checks(rs):
                            ctypes.byref(need), None) == rs.RS_ERR_INVALID
 
 
+def test_segmented_size_limits(rs):
+    L = rs.lib()
+    fn = L.rs_sort_segmented
+    fake, z = ctypes.c_void_p(1), ctypes.c_void_p(256)
+    need = ctypes.c_size_t(0)
+    # a batch may hold more keys than one sort (segments are sorted apart)
+    n = rs.RS_MAX_N + 1
+    assert fn(fake, rs.RS_KEY_U32, z, z, None, z, 4, n, z, 1000, None, None,
+              ctypes.byref(need), None) == rs.RS_OK
+    assert need.value >= 8 * n  # cell and value ping-pong buffers
+    assert fn(fake, rs.RS_KEY_U32, z, z, None, z, 4, rs.RS_MAX_SEGMENTED_N + 1, z, 1000, None,
+              None, ctypes.byref(need), None) == rs.RS_ERR_INVALID
+
+
 def test_context_needs_a_device(rs):
     import torch
     if torch.cuda.is_available():

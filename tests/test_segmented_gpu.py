@@ -121,6 +121,70 @@ def test_f32_rows_vs_numpy_stable(rs, ctx):
                           want.view(np.uint32))
 
 
+# ---- warp tier: segments of at most 63 keys are sorted by one warp each ----
+
+
+@pytest.mark.parametrize("inplace", [False, True])
+def test_warp_tier_tiny_segments_pairs(rs, ctx, oracle, inplace):
+    rng = np.random.default_rng(11)
+    sizes = rng.integers(0, 64, 5000)
+    sizes[:8] = [63, 62, 33, 32, 31, 1, 0, 2]
+    off = _offsets(sizes)
+    n = int(off[-1])
+    keys = rng.integers(0, 40, n, dtype=np.uint32)  # many ties inside each segment
+    vals = rng.integers(0, 1 << 32, n, dtype=np.uint32)
+    ref_k, perm = _oracle_segments(oracle, keys, off, oracle.sort_u32)
+    dk, dv, doff = to_dev(keys), to_dev(vals), to_dev(off)
+    if inplace:
+        rs.rs_sort_segmented(dk, doff, dv, dk, dv, ctx=ctx)
+        ko, vo = dk, dv
+    else:
+        ko, vo = rs.rs_sort_segmented(dk, doff, dv, ctx=ctx)
+    ctx.check()
+    assert np.array_equal(from_dev(ko, np.uint32), ref_k)
+    base = np.repeat(off[:-1].astype(np.int64), np.diff(off).astype(np.int64))
+    assert np.array_equal(from_dev(vo, np.uint32), vals[base + perm])
+
+
+def test_warp_tier_u64_decimal_and_argsort(rs, ctx, oracle):
+    rng = np.random.default_rng(12)
+    sizes = rng.integers(1, 64, 3000)
+    off = _offsets(sizes)
+    n = int(off[-1])
+    k64 = W.u64_keys(n, seed_extra=5)
+    k64[1::3] = k64[0::3][: k64[1::3].size]  # ties
+    ref, perm = _oracle_segments(oracle, k64, off, oracle.sort_u64)
+    ko, idx = rs.rs_sort_segmented(to_dev(k64), to_dev(off), argsort=True, ctx=ctx)
+    ctx.check()
+    assert np.array_equal(from_dev(ko, np.uint64), ref)
+    assert np.array_equal(idx.cpu().numpy(), perm)
+    dec = W.decimals(n, 3, 2, seed_extra=6)
+    ref, perm = _oracle_segments(oracle, dec, off,
+                                 lambda k: oracle.sort_fixed_decimal(k, 3, 2))
+    ko, idx = rs.rs_sort_segmented(to_dev(dec), to_dev(off), argsort=True, decimal=(3, 2),
+                                   index_dtype=torch.int32, ctx=ctx)
+    ctx.check()
+    assert np.array_equal(from_dev(ko, np.int64), ref)
+    assert np.array_equal(idx.cpu().numpy().astype(np.int64), perm)
+
+
+def test_warp_tier_uniform_rows(rs, ctx):
+    # equal segments of 50 keys (no offsets array): every row goes to the warp tier
+    rng = np.random.default_rng(13)
+    rows, length = 4000, 50
+    x = rng.standard_normal((rows, length)).astype(np.float32)
+    x[:, ::3] = np.round(x[:, ::3])  # ties
+    ko, idx = rs.rs_sort_segmented(torch.from_numpy(x).cuda().reshape(-1), None,
+                                   num_segs=rows, argsort=True, ctx=ctx)
+    ctx.check()
+    ref = np.argsort(x, axis=1, kind="stable")
+    assert np.array_equal(idx.cpu().numpy().reshape(rows, length), ref)
+    want = np.take_along_axis(x, ref, axis=1)
+    want[want == 0] = 0.0  # -0.0 is written as +0.0
+    assert np.array_equal(ko.cpu().numpy().reshape(rows, length).view(np.uint32),
+                          want.view(np.uint32))
+
+
 def test_bad_offsets_flagged(rs, ctx):
     keys = to_dev(np.arange(100, dtype=np.uint32)[::-1].copy())
     off = to_dev(np.array([0, 50, 40, 100], np.uint64))
