@@ -56,7 +56,8 @@ typedef enum rs_status {
     RS_ERR_UNSUPPORTED = 6
 } rs_status;
 
-/* Largest n any call accepts (per-tile look-back counts are 30-bit). */
+/* Largest n of one sort (per-tile look-back counts are 30-bit); a segmented
+ * batch may hold more (RS_MAX_SEGMENTED_N). */
 #define RS_MAX_N ((size_t)((1u << 30) - 1u))
 
 typedef enum rs_key_type {
@@ -84,7 +85,10 @@ typedef struct rs_ctx rs_ctx;
 
 /* Create a context bound to CUDA device `device`.  Allocates the context's
  * 256-byte device status word once (the only allocation the library makes).
- * RS_ERR_INVALID if ctx is NULL or the device does not exist. */
+ * RS_ERR_INVALID if ctx is NULL or the device does not exist.  A context
+ * keeps host-side counters and timing events: use it from one host thread at
+ * a time (one context per thread for concurrent callers; every other part of
+ * the library is safe to call from several threads). */
 rs_status rs_ctx_create(rs_ctx** ctx, int device);
 
 /* Free the context; waits for nothing (the caller must not destroy a context

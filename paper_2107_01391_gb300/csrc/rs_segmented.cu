@@ -23,6 +23,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "../../include/rs.h"
 #include "rs_sort_impl.cuh"
@@ -460,12 +461,12 @@ rs_status run_segmented(rs_ctx* ctx, const void* keys_in, void* keys_out, const 
     }
     const size_t smem = sizeof(Cell) * SEG_TILE + (kPairs ? sizeof(VS) * SEG_TILE : 0);
     auto kern = seg_sort_kernel<C, V>;
-    static bool smem_set[64] = {};
-    if (ctx->device < 64 && !smem_set[ctx->device]) {
+    static std::atomic<bool> smem_set[64];  // zero-initialised: false
+    if (ctx->device < 64 && !smem_set[ctx->device].load(std::memory_order_acquire)) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
             return RS_ERR_CUDA;
-        smem_set[ctx->device] = true;
+        smem_set[ctx->device].store(true, std::memory_order_release);
     }
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLOCK, smem) != cudaSuccess ||

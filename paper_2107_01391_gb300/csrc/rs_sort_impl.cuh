@@ -9,6 +9,7 @@
 #pragma once
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 
 #include "rs_ctx.hpp"
@@ -147,8 +148,8 @@ rs_status run_sort(rs_ctx* ctx, const void* keys_in, void* keys_out, const void*
         LaunchTimer lt(ctx, KC_HIST, stream);
         const size_t lane_hist = sizeof(Cell) == 4 ? LANE_HIST_WORDS * sizeof(uint32_t) : 0;
         const int grid = count_grid(n, sm_count(ctx->device));
-        static bool count_smem_set[64] = {};
-        if (lane_hist && ctx->device < 64 && !count_smem_set[ctx->device]) {
+        static std::atomic<bool> count_smem_set[64];  // zero-initialised: false
+        if (lane_hist && ctx->device < 64 && !count_smem_set[ctx->device].load(std::memory_order_acquire)) {
             if (cudaFuncSetAttribute(count_kernel<C, true>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)lane_hist) != cudaSuccess ||
@@ -156,7 +157,7 @@ rs_status run_sort(rs_ctx* ctx, const void* keys_in, void* keys_out, const void*
                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)lane_hist) != cudaSuccess)
                 return RS_ERR_CUDA;
-            count_smem_set[ctx->device] = true;
+            count_smem_set[ctx->device].store(true, std::memory_order_release);
         }
         if (fill_allowed)
             count_kernel<C, true><<<grid, BLOCK, lane_hist, stream>>>(a);
@@ -179,12 +180,12 @@ rs_status run_sort(rs_ctx* ctx, const void* keys_in, void* keys_out, const void*
     auto kern = pass_kernel<C, V, IPT, PB>;
     // static + dynamic shared memory may exceed the 48 KB default: opt in
     // once per device for this instantiation
-    static bool smem_set[64] = {};
-    if (ctx->device < 64 && !smem_set[ctx->device]) {
+    static std::atomic<bool> smem_set[64];  // zero-initialised: false
+    if (ctx->device < 64 && !smem_set[ctx->device].load(std::memory_order_acquire)) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)Smem::kBytes) != cudaSuccess)
             return RS_ERR_CUDA;
-        smem_set[ctx->device] = true;
+        smem_set[ctx->device].store(true, std::memory_order_release);
     }
     for (uint32_t p = 0; p < passes; p++) {
         PassArgs a{};
