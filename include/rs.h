@@ -87,8 +87,10 @@ typedef struct rs_ctx rs_ctx;
  * 256-byte device status word once (the only allocation the library makes).
  * RS_ERR_INVALID if ctx is NULL or the device does not exist.  A context
  * keeps host-side counters and timing events: use it from one host thread at
- * a time (one context per thread for concurrent callers; every other part of
- * the library is safe to call from several threads). */
+ * a time (one context per thread for concurrent callers).  Calls on
+ * different contexts may run from several threads at once, with the one
+ * exception of rs_sort_u32_noalloc, whose shared workspace serialises its
+ * callers. */
 rs_status rs_ctx_create(rs_ctx** ctx, int device);
 
 /* Free the context; waits for nothing (the caller must not destroy a context
