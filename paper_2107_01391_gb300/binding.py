@@ -255,6 +255,10 @@ def _key_type(keys: torch.Tensor, decimal: tuple[int, int] | None) -> int:
         return RS_KEY_U32
     if keys.dtype in U64_DTYPES:
         return RS_KEY_U64
+    if keys.dtype == torch.float32:
+        return RS_KEY_F32
+    if keys.dtype == torch.float64:
+        return RS_KEY_F64
     raise TypeError(f"unsupported key dtype {keys.dtype}")
 
 
@@ -264,8 +268,9 @@ def rs_sort_pairs(keys: torch.Tensor, values: torch.Tensor, keys_out: torch.Tens
     """Stable key/value sort; returns (sorted keys, values in the same order).
 
     ``decimal=(int_digits, frac_digits)`` sorts int64 keys as fixed-point
-    decimals; otherwise 4-byte keys are uint32 and 8-byte keys uint64.
-    Values may be any 4- or 8-byte dtype (moved as raw bits).
+    decimals; float32/float64 keys sort as numbers (-0.0 ties +0.0 and is
+    written as +0.0, NaNs last); other 4-byte keys are uint32 and 8-byte keys
+    uint64.  Values may be any 4- or 8-byte dtype (moved as raw bits).
     """
     kt = _key_type(keys, decimal)
     _cuda(keys, "keys", keys.element_size(), (keys.dtype,))

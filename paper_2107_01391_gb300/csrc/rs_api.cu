@@ -253,8 +253,10 @@ rs_status rs_sort_pairs(rs_ctx* ctx, rs_key_type kt, const void* keys_in, void* 
                         const rs_key_params* params, void* temp, size_t* temp_bytes,
                         rs_stream_t stream) {
     if (val_bytes != 4 && val_bytes != 8) return RS_ERR_INVALID;
-    const size_t kbytes = kt == RS_KEY_U32 ? 4 : 8;
-    if (kt != RS_KEY_U32 && kt != RS_KEY_U64 && kt != RS_KEY_I64_DEC) return RS_ERR_UNSUPPORTED;
+    const size_t kbytes = (kt == RS_KEY_U32 || kt == RS_KEY_F32) ? 4 : 8;
+    if (kt != RS_KEY_U32 && kt != RS_KEY_U64 && kt != RS_KEY_I64_DEC && kt != RS_KEY_F32 &&
+        kt != RS_KEY_F64)
+        return RS_ERR_UNSUPPORTED;
     rs_status s = check_common(ctx, keys_in, keys_out, n, kbytes, temp_bytes);
     if (s != RS_OK) return s;
     if (n > 0 && (!vals_in || !vals_out || !aligned(vals_in, val_bytes) ||
@@ -271,6 +273,14 @@ rs_status rs_sort_pairs(rs_ctx* ctx, rs_key_type kt, const void* keys_in, void* 
         if (val_bytes == 4)
             return remember(ctx, run_sort<CodecU64, uint32_t>(ctx, keys_in, keys_out, vals_in, vals_out, n, CodecParams{0}, 64, temp, temp_bytes, st));
         return remember(ctx, run_sort<CodecU64, uint64_t>(ctx, keys_in, keys_out, vals_in, vals_out, n, CodecParams{0}, 64, temp, temp_bytes, st));
+    case RS_KEY_F32:
+        if (val_bytes == 4)
+            return remember(ctx, run_sort<CodecF32, uint32_t>(ctx, keys_in, keys_out, vals_in, vals_out, n, CodecParams{0}, 32, temp, temp_bytes, st));
+        return remember(ctx, run_sort<CodecF32, uint64_t>(ctx, keys_in, keys_out, vals_in, vals_out, n, CodecParams{0}, 32, temp, temp_bytes, st));
+    case RS_KEY_F64:
+        if (val_bytes == 4)
+            return remember(ctx, run_sort<CodecF64, uint32_t>(ctx, keys_in, keys_out, vals_in, vals_out, n, CodecParams{0}, 64, temp, temp_bytes, st));
+        return remember(ctx, run_sort<CodecF64, uint64_t>(ctx, keys_in, keys_out, vals_in, vals_out, n, CodecParams{0}, 64, temp, temp_bytes, st));
     default:
         if (!params) return RS_ERR_INVALID;
         return remember(ctx, sort_decimal(ctx, static_cast<const int64_t*>(keys_in),

@@ -5,7 +5,8 @@ import torch
 
 _TO_TORCH = {np.dtype(np.uint32): np.int32, np.dtype(np.int32): np.int32,
              np.dtype(np.uint64): np.int64, np.dtype(np.int64): np.int64,
-             np.dtype(np.float32): np.float32, np.dtype(np.uint8): np.uint8}
+             np.dtype(np.float32): np.float32, np.dtype(np.float64): np.float64,
+             np.dtype(np.uint8): np.uint8}
 
 
 def to_dev(a: np.ndarray) -> torch.Tensor:

@@ -91,6 +91,11 @@ def test_argument_checks(rs):
     # unknown key type
     assert L.rs_sort_pairs(fake, 9, z, z, z, z, 4, 10, None, None, ctypes.byref(need),
                            None) == rs.RS_ERR_UNSUPPORTED
+    # float keys: a size query succeeds for both widths and payload sizes
+    for kt in (rs.RS_KEY_F32, rs.RS_KEY_F64):
+        for vb in (4, 8):
+            assert L.rs_sort_pairs(fake, kt, z, z, z, z, vb, 10, None, None,
+                                   ctypes.byref(need), None) == rs.RS_OK
     # decimal pairs need their digit counts
     assert L.rs_sort_pairs(fake, rs.RS_KEY_I64_DEC, z, z, z, z, 4, 10, None, None,
                            ctypes.byref(need), None) == rs.RS_ERR_INVALID

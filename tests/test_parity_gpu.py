@@ -309,3 +309,36 @@ def test_timing_and_launch_count(rs, ctx):
     assert launches == 4 and ms > 0
     assert ctx.launch_count() - before == 6  # count + fill + 4 passes
     ctx.set_timing(False)
+
+
+# --------------------------------------------------------------- float keys
+
+
+def _canonical(keys):
+    """What the library writes for float keys: -0.0 as +0.0, every NaN as the
+    quiet NaN of its width (the order is decided before, by the oracle)."""
+    out = keys.copy()
+    out[out == 0] = 0.0
+    out[np.isnan(out)] = np.nan
+    return out
+
+
+@pytest.mark.parametrize("fdt", [np.float32, np.float64])
+@pytest.mark.parametrize("n", [1, 7, 7168 + 3, 3 * 10240 + 17, 100_003])
+def test_float_pairs(rs, ctx, oracle, fdt, n):
+    rng = np.random.default_rng(n + (0 if fdt == np.float32 else 1))
+    keys = rng.standard_normal(n).astype(fdt)
+    keys[::5] = np.round(keys[::5])  # ties, including +0.0 and -0.0
+    special = np.array([0.0, -0.0, np.inf, -np.inf, np.nan, -np.nan, 1e-45, -1e-45], fdt)
+    m = min(n, special.size)
+    keys[rng.permutation(n)[:m]] = special[:m]
+    vals = np.arange(n, dtype=np.uint32)
+    _, perm, _ = oracle.sort_float(keys)
+    perm = perm.astype(np.int64)
+    ko, vo = rs.rs_sort_pairs(to_dev(keys), to_dev(vals), ctx=ctx)
+    ctx.check()
+    assert np.array_equal(from_dev(vo, np.uint32).astype(np.int64), perm)
+    want = _canonical(keys[perm])
+    got = from_dev(ko, fdt)
+    assert np.array_equal(got.view(np.uint32 if fdt == np.float32 else np.uint64),
+                          want.view(np.uint32 if fdt == np.float32 else np.uint64))
