@@ -131,8 +131,9 @@ rs_status rs_sort_fixed_decimal(rs_ctx* ctx, const int64_t* keys_in, int64_t* ke
 
 /* Stable key/value sort: the value at input i travels with key i.
  * kt selects the key type (params required for RS_KEY_I64_DEC, ignored
- * otherwise); val_bytes is 4 or 8.  vals_in/vals_out are device arrays of n
- * values.  Float keys (RS_KEY_F32/F64, not in the paper) are mapped to
+ * otherwise); val_bytes is 4 or 8, and vals_in/vals_out are device arrays of
+ * n values.  val_bytes == 0 with vals_in == vals_out == NULL sorts the keys
+ * alone (the keys-only form for every key type).  Float keys (RS_KEY_F32/F64, not in the paper) are mapped to
  * order-preserving unsigned cells of the same width and written back as
  * rs_key_type describes (-0.0 as +0.0, NaNs last as the quiet NaN). */
 rs_status rs_sort_pairs(rs_ctx* ctx, rs_key_type kt, const void* keys_in, void* keys_out,

@@ -262,7 +262,8 @@ def _key_type(keys: torch.Tensor, decimal: tuple[int, int] | None) -> int:
     raise TypeError(f"unsupported key dtype {keys.dtype}")
 
 
-def rs_sort_pairs(keys: torch.Tensor, values: torch.Tensor, keys_out: torch.Tensor | None = None,
+def rs_sort_pairs(keys: torch.Tensor, values: torch.Tensor | None,
+                  keys_out: torch.Tensor | None = None,
                   values_out: torch.Tensor | None = None, *, decimal: tuple[int, int] | None = None,
                   ctx: Context | None = None, stream=None, temp: torch.Tensor | None = None):
     """Stable key/value sort; returns (sorted keys, values in the same order).
@@ -270,18 +271,23 @@ def rs_sort_pairs(keys: torch.Tensor, values: torch.Tensor, keys_out: torch.Tens
     ``decimal=(int_digits, frac_digits)`` sorts int64 keys as fixed-point
     decimals; float32/float64 keys sort as numbers (-0.0 ties +0.0 and is
     written as +0.0, NaNs last); other 4-byte keys are uint32 and 8-byte keys
-    uint64.  Values may be any 4- or 8-byte dtype (moved as raw bits).
+    uint64.  Values may be any 4- or 8-byte dtype (moved as raw bits);
+    ``values=None`` sorts the keys alone and returns (sorted keys, None).
     """
     kt = _key_type(keys, decimal)
     _cuda(keys, "keys", keys.element_size(), (keys.dtype,))
-    if values.numel() != keys.numel():
-        raise ValueError("keys and values must have the same length")
-    vb = values.element_size()
-    if vb not in (4, 8):
-        raise TypeError("values must be 4 or 8 bytes per element")
-    _cuda(values, "values", vb, (values.dtype,))
+    if values is None:
+        vb = 0
+        values_out = None
+    else:
+        if values.numel() != keys.numel():
+            raise ValueError("keys and values must have the same length")
+        vb = values.element_size()
+        if vb not in (4, 8):
+            raise TypeError("values must be 4 or 8 bytes per element")
+        _cuda(values, "values", vb, (values.dtype,))
+        values_out = torch.empty_like(values) if values_out is None else values_out
     keys_out = torch.empty_like(keys) if keys_out is None else keys_out
-    values_out = torch.empty_like(values) if values_out is None else values_out
     ctx = ctx or default_context(keys.device.index)
     prm = KeyParams(*(decimal or (0, 0)))
     pp = ctypes.byref(prm)

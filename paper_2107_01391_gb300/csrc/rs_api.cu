@@ -252,18 +252,41 @@ rs_status rs_sort_pairs(rs_ctx* ctx, rs_key_type kt, const void* keys_in, void* 
                         const void* vals_in, void* vals_out, size_t val_bytes, size_t n,
                         const rs_key_params* params, void* temp, size_t* temp_bytes,
                         rs_stream_t stream) {
-    if (val_bytes != 4 && val_bytes != 8) return RS_ERR_INVALID;
+    if (val_bytes != 0 && val_bytes != 4 && val_bytes != 8) return RS_ERR_INVALID;
     const size_t kbytes = (kt == RS_KEY_U32 || kt == RS_KEY_F32) ? 4 : 8;
     if (kt != RS_KEY_U32 && kt != RS_KEY_U64 && kt != RS_KEY_I64_DEC && kt != RS_KEY_F32 &&
         kt != RS_KEY_F64)
         return RS_ERR_UNSUPPORTED;
     rs_status s = check_common(ctx, keys_in, keys_out, n, kbytes, temp_bytes);
     if (s != RS_OK) return s;
-    if (n > 0 && (!vals_in || !vals_out || !aligned(vals_in, val_bytes) ||
-                  !aligned(vals_out, val_bytes)))
-        return RS_ERR_INVALID;
-    if ((keys_in == keys_out) != (vals_in == vals_out)) return RS_ERR_INVALID;
+    if (val_bytes == 0) {
+        // keys only: no value arrays
+        if (vals_in || vals_out) return RS_ERR_INVALID;
+    } else {
+        if (n > 0 && (!vals_in || !vals_out || !aligned(vals_in, val_bytes) ||
+                      !aligned(vals_out, val_bytes)))
+            return RS_ERR_INVALID;
+        if ((keys_in == keys_out) != (vals_in == vals_out)) return RS_ERR_INVALID;
+    }
     cudaStream_t st = (cudaStream_t)stream;
+    if (val_bytes == 0) {
+        switch (kt) {
+        case RS_KEY_U32:
+            return remember(ctx, run_sort<CodecU32, NoVal>(ctx, keys_in, keys_out, nullptr, nullptr, n, CodecParams{0}, 32, temp, temp_bytes, st));
+        case RS_KEY_U64:
+            return remember(ctx, run_sort<CodecU64, NoVal>(ctx, keys_in, keys_out, nullptr, nullptr, n, CodecParams{0}, 64, temp, temp_bytes, st));
+        case RS_KEY_F32:
+            return remember(ctx, run_sort<CodecF32, NoVal>(ctx, keys_in, keys_out, nullptr, nullptr, n, CodecParams{0}, 32, temp, temp_bytes, st));
+        case RS_KEY_F64:
+            return remember(ctx, run_sort<CodecF64, NoVal>(ctx, keys_in, keys_out, nullptr, nullptr, n, CodecParams{0}, 64, temp, temp_bytes, st));
+        default:
+            if (!params) return RS_ERR_INVALID;
+            return remember(ctx, sort_decimal(ctx, static_cast<const int64_t*>(keys_in),
+                                              static_cast<int64_t*>(keys_out), nullptr, nullptr, 0,
+                                              n, params->int_digits, params->frac_digits, temp,
+                                              temp_bytes, st));
+        }
+    }
     switch (kt) {
     case RS_KEY_U32:
         if (val_bytes == 4)
