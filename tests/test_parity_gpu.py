@@ -298,6 +298,23 @@ def test_u32_pairs_full_size(rs, ctx, oracle, dist):
     torch.cuda.empty_cache()
 
 
+def test_u32_pairs_maximum_size(rs, ctx, oracle):
+    # n = RS_MAX_N: per-cell counts reach the 30-bit limit of the look-back words
+    n = rs.RS_MAX_N
+    keys, vals = W.u32_pairs(n, "uniform", seed_extra=7)
+    dk, dv = to_dev(keys), to_dev(vals)
+    ko, vo = rs.rs_sort_pairs(dk, dv, ctx=ctx)
+    ctx.check()
+    assert ctx.last_plan()["tiles"] == -(-n // TILE_KEYS[("u32", "u32")])
+    _check_stable_sort_properties(dk, ko, vo)
+    rng = np.random.default_rng(98)
+    for i in list(rng.integers(0, n, 2)) + [n - 1]:
+        r = oracle.stable_rank(keys, int(i))
+        assert int(ko[r].item()) & 0xFFFFFFFF == keys[i] and int(vo[r].item()) == i
+    del dk, dv, ko, vo
+    torch.cuda.empty_cache()
+
+
 def test_timing_and_launch_count(rs, ctx):
     keys = to_dev(W.u32_keys(1 << 20))
     ctx.set_timing(True)

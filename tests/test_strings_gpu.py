@@ -68,7 +68,8 @@ def test_strings_full_size_sampled(rs, ctx, oracle):
     assert np.array_equal(got_m, ref.astype(np.uint32))
 
 
-@pytest.mark.parametrize("case", ["binary", "prefixes", "empty_mix", "all_equal", "long"])
+@pytest.mark.parametrize("case", ["binary", "prefixes", "empty_mix", "all_equal", "long",
+                                  "maximum_length"])
 def test_edge_strings(rs, ctx, oracle, case):
     rng = np.random.default_rng(7)
     if case == "binary":      # every byte value, including 0x00 and 0xff: 9-bit symbols
@@ -82,10 +83,16 @@ def test_edge_strings(rs, ctx, oracle, case):
         strs = [b"" if rng.random() < 0.5 else b"x" * int(rng.integers(1, 4)) for _ in range(9000)]
     elif case == "all_equal":
         strs = [b"same-string"] * 12_345
-    else:                     # long strings spanning several 64-bit cells
+    elif case == "long":      # long strings spanning several 64-bit cells
         strs = [bytes(rng.integers(97, 100, int(rng.integers(30, 200))).astype(np.uint8))
                 for _ in range(5000)]
-    max_len = max(1, max(len(x) for x in strs))
+    else:                     # up to RS_MAX_STRING_LEN bytes, equal for the first 1000
+        prefix = bytes(rng.integers(97, 99, 1000).astype(np.uint8))
+        strs = [prefix + bytes(rng.integers(97, 99, int(rng.integers(0, 25))).astype(np.uint8))
+                for _ in range(3000)]
+        strs.append(prefix + b"b" * (rs.RS_MAX_STRING_LEN - 1000))
+    max_len = (rs.RS_MAX_STRING_LEN if case == "maximum_length"
+               else max(1, max(len(x) for x in strs)))
     chars, offsets = _pack(strs)
     ref, _ = oracle.sort_strings(chars, offsets.astype(np.uint64))
     got = _gpu_perm(rs, ctx, chars, offsets, max_len)
