@@ -53,6 +53,10 @@ def parse():
     ap.add_argument("--log2n", type=int, default=28)
     ap.add_argument("--no-segmented", action="store_true")
     ap.add_argument("--no-autograd", action="store_true")
+    ap.add_argument("--seg-log2n", type=int, default=28,
+                    help="Run B total keys (2^k); below 28 Run A is skipped (profiling cases)")
+    ap.add_argument("--no-per-call", action="store_true",
+                    help="skip the one-call-per-segment comparison (65536 calls)")
     ap.add_argument("--no-run-a", action="store_true",
                     help="skip the 6.2e9-key segmented run (148 GB of device memory)")
     ap.add_argument("--no-configs", action="store_true",
@@ -252,7 +256,21 @@ def _batched_segmented(binding, ctx, dk, dv, doff, ko, vo, steps, warmup, stream
     return e0.elapsed_time(e1) / steps, (ctx.launch_count() - launches0) / steps
 
 
-def segmented_leg(binding, ctx, steps: int, warmup: int, run_a: bool = True):
+SEG_ONCHIP_KEYS = 4096  # segments up to one on-chip tile are read once and written once
+
+
+def seg_alg_bytes(sizes: np.ndarray, passes: int = 4) -> int:
+    """Algorithmic bytes of a segmented u32-key + 4-byte-value sort: the warp
+    and on-chip tiers move each pair once (8 B in, 8 B out); a larger segment
+    reads its keys once to count (4 B) and moves every pair once per active
+    digit group (16 B each; all four are active for uniform keys)."""
+    small = int(sizes[sizes <= SEG_ONCHIP_KEYS].sum())
+    large = int(sizes[sizes > SEG_ONCHIP_KEYS].sum())
+    return 16 * small + (4 + 16 * passes) * large
+
+
+def segmented_leg(binding, ctx, steps: int, warmup: int, run_a: bool = True,
+                  hbm_peak: float = 0.0, total_log2: int = 28, per_call: bool = True):
     """Batched segmented sort against one call per segment, same GPU, same data.
 
     Both runs draw 65536 segment sizes log-uniform in [16, 2^20] (u32 keys,
@@ -268,7 +286,7 @@ def segmented_leg(binding, ctx, steps: int, warmup: int, run_a: bool = True):
     stream = torch.cuda.current_stream()
 
     # ---- Run B: 2^28 keys ----
-    sizes = W.segment_sizes(65536, total=1 << 28)
+    sizes = W.segment_sizes(65536, total=1 << total_log2)
     keys, vals, off = W.segments(sizes)
     n = keys.size
     dk = torch.from_numpy(keys.view(np.int32)).cuda()
@@ -277,18 +295,26 @@ def segmented_leg(binding, ctx, steps: int, warmup: int, run_a: bool = True):
     ko, vo = torch.empty_like(dk), torch.empty_like(dv)
     batched_ms, seg_launches = _batched_segmented(binding, ctx, dk, dv, doff, ko, vo, steps,
                                                   warmup, stream)
-    per_call_ms = _per_call_pairs(binding, ctx, dk, dv, ko, vo, off[:-1].astype(np.int64).tolist(),
-                                  sizes.astype(np.int64).tolist(), stream)
-    out = {"workload": "65536 segments, log-uniform sizes 16..2^20 rescaled to sum 2^28 "
-                       "(Run B), u32 keys + f32 values",
+    per_call_ms = (_per_call_pairs(binding, ctx, dk, dv, ko, vo,
+                                   off[:-1].astype(np.int64).tolist(),
+                                   sizes.astype(np.int64).tolist(), stream)
+                   if per_call else None)
+    alg = seg_alg_bytes(sizes)
+    out = {"workload": f"65536 segments, log-uniform sizes 16..2^20 rescaled to sum "
+                       f"2^{total_log2} (Run B), u32 keys + f32 values",
            "total_keys": int(n), "num_segs": int(sizes.size), "max_seg": int(sizes.max()),
+           "onchip_key_share": float(sizes[sizes <= SEG_ONCHIP_KEYS].sum() / n),
            "batched_ms": batched_ms, "batched_keys_per_s": n / (batched_ms * 1e-3),
            "batched_launches": seg_launches,
-           "per_call_ms": per_call_ms, "per_call_keys_per_s": n / (per_call_ms * 1e-3),
-           "speedup": per_call_ms / batched_ms}
+           "alg_bytes": alg, "alg_gbs": alg / (batched_ms * 1e-3) / 1e9,
+           "frac_of_measured_hbm": (alg / (batched_ms * 1e-3) / 1e9 / hbm_peak
+                                    if hbm_peak else None),
+           "per_call_ms": per_call_ms,
+           "per_call_keys_per_s": n / (per_call_ms * 1e-3) if per_call_ms else None,
+           "speedup": per_call_ms / batched_ms if per_call_ms else None}
     del dk, dv, doff, ko, vo
     torch.cuda.empty_cache()
-    if not run_a:
+    if not run_a or total_log2 != 28:
         return out
 
     # ---- Run A: the sizes as drawn ----
@@ -322,12 +348,17 @@ def segmented_leg(binding, ctx, steps: int, warmup: int, run_a: bool = True):
         assert bool((seg[1:] >= seg[:-1]).all()), "Run A segment not sorted"
     per_call_ms = _per_call_pairs(binding, ctx, dk, dv, ko, vo, off[:-1].tolist(),
                                   sizes.astype(np.int64).tolist(), stream)
+    alg = seg_alg_bytes(sizes)
     out["run_a"] = {
         "workload": "65536 segments, log-uniform sizes 16..2^20 as drawn (Run A), u32 keys "
                     "+ f32 values drawn on the device",
         "total_keys": n, "max_seg": int(sizes.max()),
         "batched_ms": batched_ms, "batched_keys_per_s": n / (batched_ms * 1e-3),
         "batched_launches": seg_launches,
+        "onchip_key_share": float(sizes[sizes <= SEG_ONCHIP_KEYS].sum() / n),
+        "alg_bytes": alg, "alg_gbs": alg / (batched_ms * 1e-3) / 1e9,
+        "frac_of_measured_hbm": (alg / (batched_ms * 1e-3) / 1e9 / hbm_peak
+                                 if hbm_peak else None),
         "per_call_ms": per_call_ms, "per_call_keys_per_s": n / (per_call_ms * 1e-3),
         "speedup": per_call_ms / batched_ms}
     del dk, dv, doff, ko, vo
@@ -666,7 +697,8 @@ def run_ours(args):
     seg = None
     if not args.no_segmented and world == 1:
         seg = segmented_leg(binding, ctx, max(1, min(args.steps, 10)), max(1, min(args.warmup, 3)),
-                            run_a=not args.no_run_a)
+                            run_a=not args.no_run_a, hbm_peak=hbm_peak,
+                            total_log2=args.seg_log2n, per_call=not args.no_per_call)
 
     agl = None
     if not args.no_autograd and world == 1:
