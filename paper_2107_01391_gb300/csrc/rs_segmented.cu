@@ -363,6 +363,7 @@ __global__ void __launch_bounds__(BLOCK, seg_ctas_per_sm<C, V>()) seg_sort_kerne
             if (vdst) vdst += lo;
             const uint32_t shift = p * RADIX_BITS;
             s_run[t] = s_hist[p][t];
+            ts.count[t] = 0;  // the first tile adds nothing to s_run
             __syncthreads();
             for (uint64_t base = 0; base < len; base += SEG_TILE) {
                 const uint32_t valid = (uint32_t)min((uint64_t)SEG_TILE, len - base);
@@ -372,7 +373,8 @@ __global__ void __launch_bounds__(BLOCK, seg_ctas_per_sm<C, V>()) seg_sort_kerne
                 else
                     load_tile<C, VS, kPairs, false>(ksrc, vsrc, base, valid, a.prm, ~0ull, k, v,
                                                     a.status);
-                rank_scatter<Cell, VS, SEG_IPT, kPairs>(k, v, valid, shift, ts, s_keys, s_vals);
+                rank_scatter<Cell, VS, SEG_IPT, kPairs>(k, v, valid, shift, ts, s_keys, s_vals,
+                                                        s_run);
                 for (uint32_t j = t; j < valid; j += BLOCK) {
                     const Cell c = s_keys[j];
                     const uint32_t d = digit_of(c, shift);
@@ -383,10 +385,13 @@ __global__ void __launch_bounds__(BLOCK, seg_ctas_per_sm<C, V>()) seg_sort_kerne
                         static_cast<Cell*>(kdst)[g] = c;
                     if constexpr (kPairs) vdst[g] = s_vals[j];
                 }
-                __syncthreads();
-                s_run[t] += ts.count[t];
-                __syncthreads();
+                // (the next tile's rank_scatter moves s_run on after its
+                // first barrier, once every thread is past this write-out)
             }
+            // the write-out above reads s_run, s_keys and ts: done before the
+            // next group resets them; also orders this group's global writes
+            // before the next group's reads
+            __syncthreads();
             src_buf = dst_buf;
             done++;
         }

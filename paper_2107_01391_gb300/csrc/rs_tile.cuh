@@ -23,10 +23,15 @@ struct TileShared {
 // Positions [0, n_valid) of the tile hold keys; the rest are ignored.
 // Returns with s_keys/s_vals holding the tile in (cell, input) order and
 // ts.count / ts.excl filled.  Every thread of the CTA must call it.
+// s_run (optional): running per-cell output offsets of a sweep over several
+// tiles; the previous tile's ts.count is added to them once every thread is
+// past its write-out (the first barrier below), so the sweep itself needs
+// no barrier between tiles.
 template <typename Cell, typename VS, int IPT, bool kPairs>
 __device__ __forceinline__ void rank_scatter(const Cell (&k)[IPT], const VS (&v)[IPT],
                                              uint32_t n_valid, uint32_t shift, TileShared& ts,
-                                             Cell* s_keys, VS* s_vals) {
+                                             Cell* s_keys, VS* s_vals,
+                                             uint32_t* s_run = nullptr) {
     const uint32_t t = threadIdx.x, lane = lane_id(), warp = t >> 5;
     const uint32_t wbase = warp * 32 * IPT;
     for (uint32_t d = lane; d < RADIX; d += 32) ts.wh[warp][d] = 0;
@@ -48,6 +53,7 @@ __device__ __forceinline__ void rank_scatter(const Cell (&k)[IPT], const VS (&v)
     const uint32_t excl = block_exclusive_scan(run, ts.warp_sum, &total);
 #pragma unroll
     for (int w = 0; w < WARPS; w++) ts.wh[w][t] += excl;
+    if (s_run) s_run[t] += ts.count[t];  // thread t owns cell t in both
     ts.count[t] = run;
     ts.excl[t] = excl;
     __syncthreads();
