@@ -176,11 +176,14 @@ rs_status rs_sort_strings(rs_ctx* ctx, const uint8_t* chars, const uint32_t* off
  * n may exceed RS_MAX_N, up to RS_MAX_SEGMENTED_N; a single segment holds at
  * most RS_MAX_SEGMENT_LEN keys.  Offsets that decrease or pass n, or a longer
  * segment, raise RS_ERR_RANGE (device-detected) and the offending segment is
- * skipped.  One launch sorts every segment, largest first: segments of at
- * most 63 keys by one warp each, of at most 4096 keys on chip by one CTA in
- * one read and one write, larger ones by one CTA each. */
+ * skipped (overlapping segments, from offsets that go back, are flagged too;
+ * their output is unspecified).  The segments are sorted largest first by
+ * one persistent launch: those of at most 63 keys by one warp each, of at
+ * most 4096 keys on chip by one CTA in one read and one write, below 2^14
+ * keys by one CTA each; longer ones by device-wide passes over all of them
+ * at once, one launch per digit group, with a look-back per segment. */
 #define RS_MAX_SEGMENTED_N (1ull << 40)
-#define RS_MAX_SEGMENT_LEN 0xffffffffull
+#define RS_MAX_SEGMENT_LEN RS_MAX_N
 rs_status rs_sort_segmented(rs_ctx* ctx, rs_key_type kt, const void* keys_in, void* keys_out,
                             const void* vals_in, void* vals_out, size_t val_bytes, size_t n,
                             const uint64_t* seg_offsets, size_t num_segs,

@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "RS_OK", 1: "RS_ERR_INVALID", 2: "RS_ERR_RANGE", 3: "RS_ERR_T
 RS_KEY_U32, RS_KEY_U64, RS_KEY_I64_DEC, RS_KEY_F32, RS_KEY_F64 = 0, 1, 2, 3, 4
 RS_MAX_N = (1 << 30) - 1
 RS_MAX_SEGMENTED_N = 1 << 40
-RS_MAX_SEGMENT_LEN = (1 << 32) - 1
+RS_MAX_SEGMENT_LEN = RS_MAX_N
 RS_FILL_CELLS = 4096
 
 # Every function the header declares (the CPU test checks the export table).

@@ -11,14 +11,25 @@
 //          after them is as small), a CTA takes eight at a time and each
 //          warp sorts one: two keys per lane, each ranked by counting the
 //          keys before it in (cell, position) order;
-//        - a segment of at most one tile is loaded once into registers and
-//          sorted entirely on chip: one rank-and-scatter through shared
-//          memory per 8-bit digit group, then one coalesced write
-//          (16 bytes per u32 key+value pair in total);
-//        - a larger segment is sorted by its CTA alone: one read to count
-//          every digit group, then per non-trivial group a sweep over the
-//          segment's tiles in input order with running cell offsets in
-//          shared memory (a CTA-sequential extraction cycle, no look-back).
+//        - a segment of at most 4096 keys (one tile) is loaded once into
+//          registers and sorted entirely on chip: one rank-and-scatter
+//          through shared memory per 8-bit digit group, then one coalesced
+//          write (16 bytes per u32 key+value pair in total);
+//        - every longer segment is first read once to count all its digit
+//          groups; a segment below 2^DEV_MIN_LOG2 keys is then sorted by its
+//          CTA alone: per non-trivial group a sweep over its tiles in input
+//          order with running cell offsets in shared memory (a
+//          CTA-sequential extraction cycle, no look-back);
+//        - a segment of 2^DEV_MIN_LOG2 keys or more (these come first in the
+//          list) leaves its groups' raster-order starts and the set of
+//          non-trivial groups in global memory for the device tier;
+//   4. seg_tiles_kernel  (before 3) gives every device-tier segment a
+//                        contiguous range of device tiles;
+//   5. seg_pass_kernel   the device tier, once per digit group: all the
+//                        tiles of all device-tier segments in one launch,
+//                        each ranked like the device-wide pass and placed
+//                        with a decoupled look-back that stops at its
+//                        segment's first tile.
 
 #include <cuda_runtime.h>
 
@@ -36,13 +47,24 @@ constexpr int SEG_IPT = 16;
 constexpr uint32_t SEG_TILE = BLOCK * SEG_IPT;
 constexpr int SIZE_CLASSES = 64;
 constexpr uint64_t WARP_SEG_MAX = 63;         // segments sorted by one warp
-constexpr uint64_t SEG_MAX_LEN = 0xffffffffull;  // counts within a segment are 32-bit
+constexpr uint64_t SEG_MAX_LEN = RS_MAX_N;  // look-back words of the device tier hold 30-bit counts
+// Segments of at least 2^DEV_MIN_LOG2 keys go to the device tier: exactly the
+// size classes 0..DEV_CLASS_MAX (class = leading zeros of the length).
+// Shorter ones above one tile are swept by one CTA.  2^14 measured best
+// (Run B / Run A / 8192-key rows, ms: 2^13 6.27 / 133.0 / 1.41, 2^14 6.12 /
+// 132.9 / 1.05, 2^15 6.21 / 133.0 / 1.04, 2^16 6.42 / 133.6 / 1.04).
+constexpr uint32_t DEV_MIN_LOG2 = 14;
+constexpr uint32_t DEV_CLASS_MAX = 63 - DEV_MIN_LOG2;
+static_assert((1u << DEV_MIN_LOG2) > SEG_TILE, "the device tier starts above the on-chip tier");
 
 struct SegControl {
     uint32_t class_count[SIZE_CLASSES];
     uint32_t class_cursor[SIZE_CLASSES];
     uint32_t work;
     uint32_t done;
+    uint32_t n_large;                  // segments of the device tier (a prefix of the order)
+    uint32_t dev_tiles;                // device tiles handed out
+    uint32_t dev_counter[MAX_PASSES];  // tile claims of each device-tier pass
 };
 
 struct SegArgs {
@@ -63,6 +85,15 @@ struct SegArgs {
     uint32_t in_is_out;
     CodecParams prm;
     uint32_t* status;
+    // device tier
+    uint32_t* bins;        // [n_large][passes][RADIX] raster-order starts within the segment
+    uint32_t* dev_use;     // [n_large] bit p: digit group p moves data
+    uint32_t* tile_start;  // [n_large] first device tile of the segment
+    uint32_t* tile_owner;  // [max_tiles] order index of the segment owning a tile
+    uint32_t* lookback[2];
+    uint64_t max_tiles;
+    uint32_t n_large_max;  // room of bins, dev_use and tile_start
+    uint32_t dev_tile;     // keys per device tile
 };
 
 // Size class: 0 holds the largest segments (2^63 and up), 63 the empty ones.
@@ -112,7 +143,36 @@ __global__ void __launch_bounds__(BLOCK) seg_size_kernel(SegArgs a) {
         for (int c = 0; c < SIZE_CLASSES; c++) {
             a.ctl->class_cursor[c] = run;
             run += __ldcg(&a.ctl->class_count[c]);
+            // (more large segments than n / 2^DEV_MIN_LOG2 only when
+            // segments overlap, which breaks the offsets' contract: it is
+            // flagged and the rest are swept by single CTAs)
+            if (c == (int)DEV_CLASS_MAX) {
+                a.ctl->n_large = min(run, a.n_large_max);
+                if (run > a.n_large_max) atomicOr(a.status, STATUS_RANGE);
+            }
         }
+    }
+}
+
+// Device tiles for the large segments (order[0 .. n_large)): each takes a
+// contiguous range of ceil(len / dev_tile) tiles from a shared counter, and
+// every tile records its owner.  Ranges come out in any order; within a
+// segment the tiles are in input order.
+__global__ void __launch_bounds__(BLOCK) seg_tiles_kernel(SegArgs a) {
+    const uint32_t n_large = __ldcg(&a.ctl->n_large);
+    for (uint64_t i = (uint64_t)blockIdx.x * BLOCK + threadIdx.x; i < n_large;
+         i += (uint64_t)gridDim.x * BLOCK) {
+        uint64_t lo, hi;
+        seg_bounds(a, a.order[i], lo, hi);  // valid: bad bounds are in the last class
+        const uint32_t tiles = (uint32_t)((hi - lo + a.dev_tile - 1) / a.dev_tile);
+        const uint32_t start = atomicAdd(&a.ctl->dev_tiles, tiles);
+        if ((uint64_t)start + tiles > a.max_tiles) {  // cannot happen: the host's bound
+            atomicOr(a.status, STATUS_RANGE);
+            a.tile_start[i] = 0xffffffffu;
+            continue;
+        }
+        a.tile_start[i] = start;
+        for (uint32_t j = 0; j < tiles; j++) a.tile_owner[start + j] = (uint32_t)i;
     }
 }
 
@@ -261,7 +321,8 @@ __global__ void __launch_bounds__(BLOCK, seg_ctas_per_sm<C, V>()) seg_sort_kerne
 
         Cell k[SEG_IPT];
         VS v[SEG_IPT];
-        if (len <= SEG_TILE) {
+        const bool device_tier = first_w < __ldcg(&a.ctl->n_large);
+        if (!device_tier && len <= SEG_TILE) {
             // ---- one tile: sorted on chip, read once and written once ----
             const uint32_t valid = (uint32_t)len;
             load_tile<C, VS, kPairs, true>(a.keys_in, vin, lo, valid, a.prm,
@@ -292,7 +353,7 @@ __global__ void __launch_bounds__(BLOCK, seg_ctas_per_sm<C, V>()) seg_sort_kerne
             continue;
         }
 
-        // ---- larger segment: count every digit group in one read ----
+        // ---- above one tile: count every digit group in one read ----
         for (uint32_t i = t; i < MAX_PASSES * RADIX; i += BLOCK) (&s_hist[0][0])[i] = 0;
         __syncthreads();
         {
@@ -314,32 +375,43 @@ __global__ void __launch_bounds__(BLOCK, seg_ctas_per_sm<C, V>()) seg_sort_kerne
             uint32_t total;
             const uint32_t e = block_exclusive_scan(h, ts.warp_sum, &total);
             const int occupied = __syncthreads_count(h != 0);
-            s_hist[p][t] = e;
+            if (device_tier)
+                a.bins[((size_t)first_w * a.passes + p) * RADIX + t] = e;
+            else
+                s_hist[p][t] = e;
             if (t == 0) s_active[p] = occupied > 1;
         }
         __syncthreads();
-        // route as the device-wide sort does: the last active group writes
-        // OUT, earlier ones alternate TMP/OUT, the first reads IN; in place
-        // needs an even count (one trivial group is re-activated), out of
-        // place at least one
-        uint32_t act = 0;
-        for (uint32_t p = 0; p < a.passes; p++) act += s_active[p];
-        bool use[MAX_PASSES];
-        for (uint32_t p = 0; p < MAX_PASSES; p++) use[p] = p < a.passes && s_active[p];
-        // (the pass count is even, so a trivial group is always there to
-        // switch on; an argsort must run at least once to write its indices)
-        uint32_t need = a.in_is_out ? (act & 1u) : (act == 0);
-        if (a.in_is_out && act == 0 && a.iota) need = 2;
-        for (uint32_t p = 0; p < a.passes && need; p++)
-            if (!use[p]) {
-                use[p] = true;
-                act++;
-                need--;
-            }
+        // route as the device-wide sort does: the last moving group writes OUT,
+        // earlier ones alternate TMP/OUT, the first reads IN; in place needs an
+        // even count of moving groups (a trivial one is switched back on), out
+        // of place at least one (two for an in-place argsort, which must write
+        // its indices); the pass count is even, so a trivial group is there
+        uint32_t use = 0;
+        for (uint32_t p = 0; p < a.passes; p++) use |= (s_active[p] ? 1u : 0u) << p;
+        {
+            const uint32_t act = __popc(use);
+            uint32_t need = a.in_is_out ? (act & 1u) : (act == 0);
+            if (a.in_is_out && act == 0 && a.iota) need = 2;
+            for (uint32_t p = 0; p < a.passes && need; p++)
+                if (!(use >> p & 1u)) {
+                    use |= 1u << p;
+                    need--;
+                }
+        }
+        if (device_tier) {
+            // the device tier moves this segment: its starts are stored above
+            if (t == 0) a.dev_use[first_w] = use;
+            continue;  // (s_hist is cleared again after the next loop-top barrier)
+        }
+
+        // ---- swept by this CTA: per moving group, the segment's tiles in
+        // input order with running cell offsets in shared memory ----
+        const uint32_t act = __popc(use);
         uint32_t done = 0;
         uint32_t src_buf = BUF_IN;
         for (uint32_t p = 0; p < a.passes; p++) {
-            if (!use[p]) continue;
+            if (!(use >> p & 1u)) continue;
             const uint32_t from_end = act - 1 - done;
             const uint32_t dst_buf = (from_end & 1u) ? BUF_TMP : BUF_OUT;
             const bool first = done == 0, last = from_end == 0;
@@ -395,14 +467,237 @@ __global__ void __launch_bounds__(BLOCK, seg_ctas_per_sm<C, V>()) seg_sort_kerne
             src_buf = dst_buf;
             done++;
         }
-        // make this CTA's writes visible before the next segment reuses smem
-        __syncthreads();
     }
 }
 
-size_t seg_workspace(size_t n, size_t num_segs, size_t cell_bytes, size_t val_bytes) {
-    return align_up(sizeof(SegControl)) + align_up(sizeof(uint32_t) * std::max<size_t>(num_segs, 1)) +
-           align_up(cell_bytes * std::max<size_t>(n, 1)) + align_up(val_bytes * std::max<size_t>(n, 1));
+// The device tier: one digit group over every tile of every segment of at
+// least SEG_TILE keys.  Persistent CTAs claim device tiles in order from a
+// counter, one claim per tile; a tile covers dev_tile consecutive keys of one
+// segment.  Like the device-wide pass it counts, publishes its per-cell
+// aggregate, ranks in (cell, input) order through shared memory, looks back
+// for the counts of the segment's earlier tiles and writes out.  A segment's
+// first tile publishes an inclusive prefix, so no look-back walks into
+// another segment.  Groups that move no data for a segment (dev_use) are
+// skipped, and its buffers alternate over the moving groups only.
+// (two CTAs per SM for every shape: the segment bookkeeping of the
+// persistent loop does not fit the 80 registers of three)
+template <class C, typename V, int IPT>
+__global__ void __launch_bounds__(BLOCK, 2) seg_pass_kernel(SegArgs a, uint32_t pass) {
+    using Cell = typename C::Cell;
+    using In = typename C::In;
+    using Out = typename C::Out;
+    constexpr bool kPairs = ValTraits<V>::kPairs;
+    constexpr uint32_t TILE = BLOCK * IPT;
+    using VS = typename std::conditional<kPairs, V, uint32_t>::type;
+
+    __shared__ uint32_t ws[WARPS][RADIX];  // per-warp counts, then next positions
+    __shared__ uint32_t s_bin[RADIX];      // segment position of tile-local index 0, per cell
+    __shared__ uint32_t s_warp[WARPS];
+    __shared__ uint32_t s_tile;
+    extern __shared__ __align__(16) unsigned char smem_dyn[];
+    Cell* s_keys = reinterpret_cast<Cell*>(smem_dyn);
+    VS* s_vals = reinterpret_cast<VS*>(smem_dyn + sizeof(Cell) * TILE);
+
+    const uint32_t t = threadIdx.x, lane = lane_id(), warp = t >> 5;
+    const uint32_t lt_mask = lanemask_lt(), gt_mask = lanemask_gt();
+    const uint32_t n_large = __ldcg(&a.ctl->n_large);
+    const uint32_t dev_tiles = (uint32_t)min((uint64_t)__ldcg(&a.ctl->dev_tiles), a.max_tiles);
+    uint32_t* const lookback = a.lookback[pass & 1];
+    uint32_t* const lookback_next = a.lookback[(pass + 1) & 1];
+    const uint32_t shift = pass * RADIX_BITS;
+
+    while (true) {
+        if (t == 0) s_tile = atomicAdd(&a.ctl->dev_counter[pass], 1u);
+        for (uint32_t d = lane; d < RADIX; d += 32) ws[warp][d] = 0;
+        __syncthreads();
+        const uint32_t g = s_tile;
+        if (g >= dev_tiles) return;
+        lookback_next[(uint64_t)g * RADIX + t] = 0;  // the next group's row of this tile
+        // the owner; every thread reads the same words, so the tests are uniform
+        const uint32_t slot = a.tile_owner[g];
+        uint64_t lo = 0, hi = 0;
+        uint32_t first_tile = 0, use = 0;
+        bool ok = slot < n_large;
+        if (ok) {
+            first_tile = a.tile_start[slot];
+            use = a.dev_use[slot];
+            ok = seg_bounds(a, a.order[slot], lo, hi) && first_tile != 0xffffffffu &&
+                 g >= first_tile && (uint64_t)(g - first_tile) * TILE < hi - lo;
+        }
+        if (!ok || !(use >> pass & 1u)) {
+            __syncthreads();  // everyone has read s_tile before the next claim
+            continue;
+        }
+        const uint32_t lt = g - first_tile;  // tile index within the segment
+        const uint64_t len = hi - lo;
+        const uint64_t tbase = (uint64_t)lt * TILE;
+        const bool full = tbase + TILE <= len;
+        const uint32_t valid = full ? TILE : (uint32_t)(len - tbase);
+        const uint32_t from_end = __popc(use) - 1 - __popc(use & ((1u << pass) - 1u));
+        const bool first = (use & ((1u << pass) - 1u)) == 0, last = from_end == 0;
+        const uint32_t dstb = (from_end & 1u) ? BUF_TMP : BUF_OUT;
+        const uint32_t srcb = first ? BUF_IN : (((from_end + 1) & 1u) ? BUF_TMP : BUF_OUT);
+        // Every buffer is addressed from the segment's start.  Cells parked in
+        // OUT live inside the segment's byte range of OUT (a cell may be
+        // narrower than an output key).
+        Cell* const tmp_cells = static_cast<Cell*>(a.keys_tmp) + lo;
+        Cell* const out_cells =
+            reinterpret_cast<Cell*>(static_cast<unsigned char*>(a.keys_out) + lo * sizeof(Out));
+
+        // ---- load (warp-striped: warp w owns tile items [w*32*IPT, (w+1)*32*IPT)) ----
+        const uint32_t w0 = warp * 32 * IPT + lane;
+        Cell k[IPT];
+        VS v[IPT];
+        if (srcb == BUF_IN) {
+            const In* in = static_cast<const In*>(a.keys_in) + lo + tbase + w0;
+            bool okd = true;  // range errors were recorded when the segment was counted
+            if (full) {
+#pragma unroll
+                for (int i = 0; i < IPT; i++) k[i] = C::decode(__ldcs(&in[i * 32]), a.prm, okd);
+            } else {
+#pragma unroll
+                for (int i = 0; i < IPT; i++)
+                    k[i] = w0 + i * 32 < valid ? C::decode(__ldcs(&in[i * 32]), a.prm, okd)
+                                               : ~Cell(0);
+            }
+        } else {
+            const Cell* in = (srcb == BUF_TMP ? tmp_cells : out_cells) + tbase + w0;
+            if (full) {
+#pragma unroll
+                for (int i = 0; i < IPT; i++) k[i] = __ldcs(&in[i * 32]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < IPT; i++) k[i] = w0 + i * 32 < valid ? __ldcs(&in[i * 32]) : ~Cell(0);
+            }
+        }
+        if constexpr (kPairs) {
+            if (first && a.iota) {
+#pragma unroll
+                for (int i = 0; i < IPT; i++) v[i] = (VS)(tbase + w0 + i * 32);
+            } else {
+                const VS* vin = static_cast<const VS*>(srcb == BUF_IN ? a.vals_in
+                                                       : (srcb == BUF_TMP ? a.vals_tmp : a.vals_out)) +
+                                lo + tbase + w0;
+                if (full) {
+#pragma unroll
+                    for (int i = 0; i < IPT; i++) v[i] = __ldcs(&vin[i * 32]);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < IPT; i++) v[i] = w0 + i * 32 < valid ? __ldcs(&vin[i * 32]) : VS(0);
+                }
+            }
+        }
+
+        // ---- counts per (warp, cell), the tile's aggregate, tile-local starts ----
+#pragma unroll
+        for (int i = 0; i < IPT; i++) atomicAdd(&ws[warp][digit_of(k[i], shift)], 1u);
+        __syncthreads();
+        const uint32_t d = t;  // this thread's cell
+        uint32_t run = 0;
+#pragma unroll
+        for (int w = 0; w < WARPS; w++) {
+            const uint32_t x = ws[w][d];
+            ws[w][d] = run;
+            run += x;
+        }
+        // padding items carry cell ~0 (digit 255) and sit after every real item
+        const uint32_t count = d == RADIX - 1 ? run - (TILE - valid) : run;
+        uint32_t* lb = lookback + (uint64_t)g * RADIX;
+        st_relaxed(&lb[d], (lt == 0 ? LB_INCLUSIVE : LB_AGGREGATE) | count);
+        uint32_t tile_total;
+        const uint32_t excl = block_exclusive_scan_n<WARPS>(count, s_warp, &tile_total);
+#pragma unroll
+        for (int w = 0; w < WARPS; w++) ws[w][d] += excl;
+        __syncthreads();
+
+        // ---- stable rank in (cell, input) order, scattered into shared memory ----
+#pragma unroll
+        for (int i = 0; i < IPT; i++) {
+            const uint32_t dk = digit_of(k[i], shift);
+            const uint32_t peers = match_digit(dk);
+            uint32_t* slot_p = &ws[warp][dk];
+            const uint32_t pos0 = *slot_p;
+            const uint32_t below = __popc(peers & lt_mask);
+            __syncwarp();
+            if ((peers & gt_mask) == 0) *slot_p = pos0 + below + 1;
+            const uint32_t pos = pos0 + below;
+            s_keys[pos] = k[i];
+            if constexpr (kPairs) s_vals[pos] = v[i];
+            __syncwarp();
+        }
+
+        // ---- look-back over the segment's earlier tiles ----
+        uint32_t before = 0;
+        if (lt > 0) {
+            const uint32_t cell[1] = {d};
+            uint32_t bf[1];
+            lookback_cells<1>(lookback, g, cell, a.status, bf);
+            before = bf[0];
+            st_relaxed(&lb[d], LB_INCLUSIVE | ((before + count) & LB_VALUE));
+        }
+        s_bin[d] = a.bins[((size_t)slot * a.passes + pass) * RADIX + d] + before - excl;
+        __syncthreads();
+
+        // ---- coalesced write-out within the segment ----
+        // (the clamp only acts after a timed-out wait: output unspecified)
+        const uint32_t gmax = (uint32_t)(len - 1);
+        if (last) {
+            Out* out = static_cast<Out*>(a.keys_out) + lo;
+            VS* vout = kPairs ? static_cast<VS*>(a.vals_out) + lo : nullptr;
+            for (uint32_t j = t; j < valid; j += BLOCK) {
+                const Cell c = s_keys[j];
+                const uint32_t gp = min(s_bin[digit_of(c, shift)] + j, gmax);
+                __stcs(&out[gp], C::encode(c, a.prm));
+                if constexpr (kPairs) __stcs(&vout[gp], s_vals[j]);
+            }
+        } else {
+            Cell* out = dstb == BUF_TMP ? tmp_cells : out_cells;
+            VS* vout = kPairs ? static_cast<VS*>(dstb == BUF_TMP ? a.vals_tmp : a.vals_out) + lo
+                              : nullptr;
+            for (uint32_t j = t; j < valid; j += BLOCK) {
+                const Cell c = s_keys[j];
+                const uint32_t gp = min(s_bin[digit_of(c, shift)] + j, gmax);
+                out[gp] = c;
+                if constexpr (kPairs) vout[gp] = s_vals[j];
+            }
+        }
+        __syncthreads();  // s_keys, s_bin and s_tile are reused by the next tile
+    }
+}
+
+// Workspace of one segmented call.  The device tier needs, per possible
+// large segment (at most n / SEG_TILE of them), the group starts and the
+// moving-group mask, and per possible device tile (a large segment of len
+// keys has ceil(len / dev_tile) <= len / dev_tile + 1 of them) an owner and
+// two look-back rows.
+struct SegLayout {
+    size_t ctl, order, keys_tmp, vals_tmp, bins, dev_use, tile_start, tile_owner, lookback0,
+        lookback1, total;
+    size_t n_large_max, max_tiles;
+};
+
+inline SegLayout seg_layout(size_t n, size_t num_segs, bool equal_segments, size_t cell_bytes,
+                            size_t val_bytes, uint32_t passes, uint32_t dev_tile) {
+    SegLayout L{};
+    // equal segments: the host knows whether any reaches the device tier
+    const bool device_tier = equal_segments
+                                 ? num_segs && (n / num_segs) >= ((size_t)1 << DEV_MIN_LOG2)
+                                 : true;
+    L.n_large_max = device_tier ? std::min<size_t>(num_segs, n >> DEV_MIN_LOG2) : 0;
+    L.max_tiles = L.n_large_max ? (n + dev_tile - 1) / dev_tile + L.n_large_max : 0;
+    size_t at = 0;
+    L.ctl = at;         at += align_up(sizeof(SegControl));
+    L.order = at;       at += align_up(sizeof(uint32_t) * std::max<size_t>(num_segs, 1));
+    L.keys_tmp = at;    at += align_up(cell_bytes * std::max<size_t>(n, 1));
+    L.vals_tmp = at;    at += align_up(val_bytes * std::max<size_t>(n, 1));
+    L.bins = at;        at += align_up(sizeof(uint32_t) * L.n_large_max * passes * RADIX);
+    L.dev_use = at;     at += align_up(sizeof(uint32_t) * L.n_large_max);
+    L.tile_start = at;  at += align_up(sizeof(uint32_t) * L.n_large_max);
+    L.tile_owner = at;  at += align_up(sizeof(uint32_t) * L.max_tiles);
+    L.lookback0 = at;   at += align_up(sizeof(uint32_t) * RADIX * L.max_tiles);
+    L.lookback1 = at;   at += align_up(sizeof(uint32_t) * RADIX * L.max_tiles);
+    L.total = at;
+    return L;
 }
 
 template <class C, typename V>
@@ -414,27 +709,32 @@ rs_status run_segmented(rs_ctx* ctx, const void* keys_in, void* keys_out, const 
     constexpr bool kPairs = ValTraits<V>::kPairs;
     using VS = typename std::conditional<kPairs, V, uint32_t>::type;
     const size_t vbytes = kPairs ? sizeof(V) : 0;
-    const size_t total = seg_workspace(n, num_segs, sizeof(Cell), vbytes);
+    constexpr int DIPT = ipt_for<C, V>();
+    constexpr uint32_t DTILE = BLOCK * DIPT;
+    const uint32_t passes = passes_for(cell_bits);
+    const SegLayout L = seg_layout(n, num_segs, seg_offsets == nullptr, sizeof(Cell), vbytes,
+                                   passes, DTILE);
     if (!temp) {
-        *temp_bytes = total;
+        *temp_bytes = L.total;
         return RS_OK;
     }
-    if (*temp_bytes < total) return RS_ERR_TEMP_TOO_SMALL;
+    if (*temp_bytes < L.total) return RS_ERR_TEMP_TOO_SMALL;
     if (reinterpret_cast<uintptr_t>(temp) % 256) return RS_ERR_INVALID;
     if (num_segs == 0 || n == 0) return RS_OK;
     DeviceGuard dg(ctx->device);
     if (!dg.ok) return RS_ERR_CUDA;
     unsigned char* T = static_cast<unsigned char*>(temp);
-    size_t at = 0;
-    SegControl* ctl = reinterpret_cast<SegControl*>(T + at);
-    at += align_up(sizeof(SegControl));
-    uint32_t* order = reinterpret_cast<uint32_t*>(T + at);
-    at += align_up(sizeof(uint32_t) * num_segs);
-    void* keys_tmp = T + at;
-    at += align_up(sizeof(Cell) * n);
-    void* vals_tmp = kPairs ? (void*)(T + at) : nullptr;
+    SegControl* ctl = reinterpret_cast<SegControl*>(T + L.ctl);
+    uint32_t* order = reinterpret_cast<uint32_t*>(T + L.order);
+    void* keys_tmp = T + L.keys_tmp;
+    void* vals_tmp = kPairs ? (void*)(T + L.vals_tmp) : nullptr;
 
     if (cudaMemsetAsync(ctl, 0, sizeof(SegControl), st) != cudaSuccess) return RS_ERR_CUDA;
+    // the device tier's first look-back buffer starts zeroed; each of its
+    // passes clears the other buffer's rows for the next one
+    if (L.max_tiles &&
+        cudaMemsetAsync(T + L.lookback0, 0, sizeof(uint32_t) * RADIX * L.max_tiles, st) != cudaSuccess)
+        return RS_ERR_CUDA;
     SegArgs a{};
     a.keys_in = keys_in;
     a.keys_out = keys_out;
@@ -449,10 +749,19 @@ rs_status run_segmented(rs_ctx* ctx, const void* keys_in, void* keys_out, const 
     a.iota = iota;
     a.order = order;
     a.ctl = ctl;
-    a.passes = passes_for(cell_bits);
+    a.passes = passes;
     a.in_is_out = keys_in == keys_out;
     a.prm = prm;
     a.status = ctx->d_status;
+    a.bins = reinterpret_cast<uint32_t*>(T + L.bins);
+    a.dev_use = reinterpret_cast<uint32_t*>(T + L.dev_use);
+    a.tile_start = reinterpret_cast<uint32_t*>(T + L.tile_start);
+    a.tile_owner = reinterpret_cast<uint32_t*>(T + L.tile_owner);
+    a.lookback[0] = reinterpret_cast<uint32_t*>(T + L.lookback0);
+    a.lookback[1] = reinterpret_cast<uint32_t*>(T + L.lookback1);
+    a.max_tiles = L.max_tiles;
+    a.n_large_max = (uint32_t)L.n_large_max;
+    a.dev_tile = DTILE;
     const int sms = sm_count(ctx->device);
     const int grid_s = (int)std::max<size_t>(1, std::min<size_t>((num_segs + BLOCK - 1) / BLOCK,
                                                                  (size_t)sms * 4));
@@ -463,6 +772,10 @@ rs_status run_segmented(rs_ctx* ctx, const void* keys_in, void* keys_out, const 
     {
         LaunchTimer lt(ctx, KC_SEG, st);
         seg_order_kernel<<<grid_s, BLOCK, 0, st>>>(a, order);
+    }
+    if (L.n_large_max) {
+        LaunchTimer lt(ctx, KC_SEG, st);
+        seg_tiles_kernel<<<grid_s, BLOCK, 0, st>>>(a);
     }
     const size_t smem = sizeof(Cell) * SEG_TILE + (kPairs ? sizeof(VS) * SEG_TILE : 0);
     auto kern = seg_sort_kernel<C, V>;
@@ -481,6 +794,34 @@ rs_status run_segmented(rs_ctx* ctx, const void* keys_in, void* keys_out, const 
     {
         LaunchTimer lt(ctx, KC_SEG, st);
         kern<<<grid, BLOCK, smem, st>>>(a);
+    }
+    if (L.n_large_max) {
+        // the device tier: one launch per digit group over all large segments
+        using DSmem = PassSmem<Cell, V, DIPT>;
+        auto dkern = seg_pass_kernel<C, V, DIPT>;
+        static std::atomic<bool> dsmem_set[64];  // zero-initialised: false
+        if (ctx->device < 64 && !dsmem_set[ctx->device].load(std::memory_order_acquire)) {
+            if (cudaFuncSetAttribute(dkern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)DSmem::kBytes) != cudaSuccess)
+                return RS_ERR_CUDA;
+            dsmem_set[ctx->device].store(true, std::memory_order_release);
+        }
+        static int dper_sm[64] = {};
+        int dper_local = 0;
+        int& dps = ctx->device < 64 ? dper_sm[ctx->device] : dper_local;
+        if (dps <= 0) {
+            int occ = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dkern, BLOCK, DSmem::kBytes) !=
+                    cudaSuccess ||
+                occ < 1)
+                occ = 1;
+            dps = occ;
+        }
+        const int dgrid = (int)std::min<size_t>((size_t)sms * dps, L.max_tiles);
+        for (uint32_t p = 0; p < passes; p++) {
+            LaunchTimer lt(ctx, KC_SEG, st);
+            dkern<<<dgrid, BLOCK, DSmem::kBytes, st>>>(a, p);
+        }
     }
     return cudaGetLastError() == cudaSuccess ? RS_OK : RS_ERR_CUDA;
 }

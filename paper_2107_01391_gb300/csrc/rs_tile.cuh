@@ -5,8 +5,8 @@
 // order.  rank_scatter() counts the tile's keys per cell (the hashing cycle
 // on one digit group, §3.1), turns the counts into raster-order starts (the
 // extraction cycle's cursor, §3.2), and writes every key (and value) to its
-// stable position in shared memory.  Used by the segmented sort, where a CTA
-// owns a whole segment and needs no look-back between tiles.
+// stable position in shared memory.  Used by the segmented sort's CTA tiers,
+// where a CTA owns a whole segment and needs no look-back between tiles.
 #pragma once
 
 #include "rs_device.cuh"

@@ -192,6 +192,17 @@ def test_bad_offsets_flagged(rs, ctx):
     assert ctx.status(True) == rs.RS_ERR_RANGE
 
 
+def test_overlapping_offsets_flagged(rs, ctx):
+    # offsets that go back make segments overlap (outside the contract): more
+    # large segments than the workspace was sized for; the extra one is
+    # flagged and skipped, nothing is accessed out of bounds
+    n = 8192
+    keys = to_dev(np.arange(n, dtype=np.uint32)[::-1].copy())
+    off = to_dev(np.array([0, n, 0, n, 0, n], np.uint64))
+    rs.rs_sort_segmented(keys, off, ctx=ctx)
+    assert ctx.status(True) == rs.RS_ERR_RANGE
+
+
 def test_run_b_full_size(rs, ctx):
     # 65536 segments, log-uniform sizes scaled to a total of 2^28 keys
     sizes = W.segment_sizes(65536, total=1 << 28)
