@@ -191,17 +191,60 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def cpu_baseline(sample_n: int):
-    """The oracle, as it stands, on the first sample_n pairs of the workload."""
+def cpu_baseline(sample_n: int, other_workloads: bool = True):
+    """The oracle, as it stands, on the first sample_n pairs of the headline
+    workload; then, beside each other workload, on a bounded sample of it."""
     from oracle import oracle
     from paper_2107_01391_gb300 import workloads as W
+
+    def timed(fn):
+        t0 = time.perf_counter()
+        fn()
+        return time.perf_counter() - t0
+
     keys, vals = W.u32_pairs(sample_n, "uniform")
-    t0 = time.perf_counter()
-    oracle.sort_pairs(keys, vals)
-    dt = time.perf_counter() - t0
-    return {"value": sample_n / dt, "unit": "keys/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {sample_n} keys (2^{int(np.log2(sample_n))}) of the uniform "
-                      f"u32-pairs workload, one oracle call, {dt:.2f} s single-threaded"}
+    dt = timed(lambda: oracle.sort_pairs(keys, vals))
+    out = {"value": sample_n / dt, "unit": "keys/s", "cores": 1, "kind": "oracle",
+           "sample": f"first {sample_n} keys (2^{int(np.log2(sample_n))}) of the uniform "
+                     f"u32-pairs workload, one oracle call, {dt:.2f} s single-threaded"}
+    del keys, vals
+    if not other_workloads:
+        return out
+    rates = {}
+
+    def rate(name, n, fn, what):
+        dt = timed(fn)
+        rates[name] = {"keys_per_s": n / dt, "sample": f"{what}, {dt:.2f} s"}
+
+    k1 = W.digits3(1 << 20)
+    rate("digits3_2p20", k1.size, lambda: oracle.sort_u32(k1), "the whole 2^20-key workload")
+    k3 = W.decimals(1 << 22, 6, 3)
+    rate("decimal_2p26", k3.size, lambda: oracle.sort_fixed_decimal(k3, 6, 3),
+         "first 2^22 keys of the 2^26-key workload")
+    chars, offs = W.strings(1 << 20)
+    rate("strings_2p24", 1 << 20,
+         lambda: oracle.sort_strings(chars, offs.astype(np.uint64), 16),
+         "2^20 strings drawn like the 2^24-string workload")
+    sizes = W.segment_sizes(65536, total=1 << 28)
+    sk, sv, soff = W.segments(sizes)
+    first = int(np.searchsorted(soff, 1 << 22))  # the first segments, about 2^22 keys
+
+    def seg():
+        for s_ in range(first):
+            lo, hi = int(soff[s_]), int(soff[s_ + 1])
+            oracle.sort_pairs(sk[lo:hi], sv[lo:hi].view(np.uint32))
+
+    rate("segmented_runB", int(soff[first]), seg,
+         f"the first {first} segments of Run B, one oracle call each")
+    rows = W.distinct_rows(64, 8192)
+
+    def ag():
+        for r in rows:
+            oracle.sort_float(r)
+
+    rate("autograd_rows", rows.size, ag, "64 of the 4096 rows of 8192 float32 keys")
+    out["other_workloads"] = rates
+    return out
 
 
 def _per_call_pairs(binding, ctx, dk, dv, ko, vo, starts, lens, stream):
