@@ -191,6 +191,17 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+# The five data cases of the paper's Table 1: decimals in [lo, hi) with cd
+# digits after the decimal point.
+TABLE1_CASES = ((1, 10, 0), (1, 10, 1), (1, 10, 2), (1, 100, 0), (1, 100, 1))
+
+
+def table1_keys(lo: int, hi: int, cd: int, n: int) -> np.ndarray:
+    """n fixed-point keys in [lo, hi) with cd fraction digits, scaled by 10^cd."""
+    rng = np.random.default_rng(20210703 + 100 * cd + hi + n)
+    return rng.integers(lo * 10 ** cd, hi * 10 ** cd, n).astype(np.int64)
+
+
 def cpu_baseline(sample_n: int, other_workloads: bool = True):
     """The oracle, as it stands, on the first sample_n pairs of the headline
     workload; then, beside each other workload, on a bounded sample of it."""
@@ -207,6 +218,10 @@ def cpu_baseline(sample_n: int, other_workloads: bool = True):
     out = {"value": sample_n / dt, "unit": "keys/s", "cores": 1, "kind": "oracle",
            "sample": f"first {sample_n} keys (2^{int(np.log2(sample_n))}) of the uniform "
                      f"u32-pairs workload, one oracle call, {dt:.2f} s single-threaded"}
+    # a library stable sort on the same sample, for context
+    dt_lib = timed(lambda: vals[np.argsort(keys, kind="stable")])
+    out["library_stable_sort"] = {"keys_per_s": sample_n / dt_lib, "cores": 1,
+                                  "what": "numpy argsort(kind='stable') + gather, same sample"}
     del keys, vals
     if not other_workloads:
         return out
@@ -236,6 +251,29 @@ def cpu_baseline(sample_n: int, other_workloads: bool = True):
 
     rate("segmented_runB", int(soff[first]), seg,
          f"the first {first} segments of Run B, one oracle call each")
+    # the same segments over every host core (the oracle's C calls release the GIL)
+    from concurrent.futures import ThreadPoolExecutor
+    threads = os.cpu_count() or 1
+
+    def one(s_):
+        lo, hi = int(soff[s_]), int(soff[s_ + 1])
+        oracle.sort_pairs(sk[lo:hi], sv[lo:hi].view(np.uint32))
+
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        dtp = timed(lambda: list(ex.map(one, range(first))))
+    rates["segmented_runB_parallel"] = {
+        "keys_per_s": int(soff[first]) / dtp, "cores": threads,
+        "sample": f"the same {first} segments, {threads} threads, {dtp:.2f} s"}
+    # the paper's Table 1 cases: decimals in [lo, hi) with cd fraction digits
+    t1 = {}
+    for (lo_, hi_, cd) in TABLE1_CASES:
+        for n_ in (10, 100, 1000, 10000):
+            keys1 = table1_keys(lo_, hi_, cd, n_)
+            d1 = len(str(hi_ - 1))
+            reps = max(1, 20000 // n_)
+            dt1 = timed(lambda: [oracle.sort_fixed_decimal(keys1, d1, cd) for _ in range(reps)])
+            t1[f"TFD({lo_},{hi_})&cd={cd} n={n_}"] = dt1 / reps
+    out["table1_oracle_s"] = t1
     rows = W.distinct_rows(64, 8192)
 
     def ag():
@@ -484,6 +522,23 @@ def configs_leg(binding, ctx, steps: int, warmup: int, hbm_peak: float):
         "matches_torch_sort": ok1,
         "note": "L2-resident and launch-bound: no roofline claim; cold/warm/graph are device "
                 "time, python_loop_us is back-to-back calls from Python (host-bound)"}
+
+    # ---- the paper's Table 1 cases (n = 10 .. 10^4): launch-bound ----
+    t1 = {}
+    for (lo_, hi_, cd) in TABLE1_CASES:
+        for n_ in (10, 100, 1000, 10000):
+            k = torch.from_numpy(table1_keys(lo_, hi_, cd, n_)).cuda()
+            d1 = len(str(hi_ - 1))
+            o = torch.empty_like(k)
+            tt = torch.empty(binding.workspace_bytes("rs_sort_fixed_decimal", n_, int_digits=d1,
+                                                     frac_digits=cd),
+                             dtype=torch.uint8, device="cuda")
+            fn = lambda: binding.rs_sort_fixed_decimal(k, d1, cd, o, ctx=ctx, temp=tt)  # noqa: E731
+            fn()
+            t1[f"TFD({lo_},{hi_})&cd={cd} n={n_}"] = timed(fn, 5) * 1e3  # us
+            assert torch.equal(o, torch.sort(k).values)
+    ctx.check()
+    out["table1_gpu_us"] = t1
 
     # ---- 2^26 signed fixed-point decimals ----
     n3 = 1 << 26
