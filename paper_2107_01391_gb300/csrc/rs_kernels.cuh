@@ -52,7 +52,7 @@ struct CountArgs {
 // (group g, cell d, lane l): ((g * RADIX/2 + d/2) * 32 + l); half = d & 1.
 // A CTA counts fewer than 32 * 65535 keys per lane copy (n < 2^30 over at
 // least min(n / 16384, 8 per SM) CTAs), so the halves cannot overflow.
-constexpr uint32_t LANE_HIST_WORDS = 4 * (RADIX / 2) * 32;  // four groups of a 32-bit cell
+constexpr uint32_t LANE_HIST_WORDS = 2 * RADIX * 32;  // four groups of a 32-bit cell, two per word
 
 template <class C, bool kFill>
 __device__ __forceinline__ void count_one(typename C::In key, const CountArgs& a,
@@ -63,11 +63,16 @@ __device__ __forceinline__ void count_one(typename C::In key, const CountArgs& a
     // every byte of the cell is counted (a group beyond the key's passes is
     // never read by the plan); unrolled, no per-group test
     if constexpr (sizeof(Cell) == 4) {
-#pragma unroll
-        for (uint32_t p = 0; p < 4; p++) {
-            const uint32_t d = digit_of(cell, p * RADIX_BITS);
-            atomicAdd(&lh[((p * (RADIX / 2) + (d >> 1)) << 5) + lane], 1u << ((d & 1u) << 4));
-        }
+        // groups 2q and 2q+1 share the word of (pair q, cell, lane): the low
+        // half counts group 2q, the high half group 2q+1, so each group's
+        // increment is a constant and its word offset is its byte of the
+        // cell times 32 (one shift and one mask)
+        const uint32_t c = (uint32_t)cell;
+        uint32_t* const w = lh + lane;
+        atomicAdd(w + ((c << 5) & 0x1FE0u), 1u);
+        atomicAdd(w + ((c >> 3) & 0x1FE0u), 0x10000u);
+        atomicAdd(w + RADIX * 32 + ((c >> 11) & 0x1FE0u), 1u);
+        atomicAdd(w + RADIX * 32 + ((c >> 19) & 0x1FE0u), 0x10000u);
     } else {
 #pragma unroll
         for (uint32_t p = 0; p < sizeof(Cell); p++)
@@ -220,10 +225,10 @@ __global__ void __launch_bounds__(BLOCK) count_kernel(CountArgs a) {
     if (kFill && big) a.plan->fill_impossible = 1;
     __syncthreads();
     if constexpr (kLaneHist) {
-        // fold the 32 lane copies: one row (group, cell pair) per warp step,
+        // fold the 32 lane copies: one row (group pair, cell) per warp step,
         // lane l reads the copy in bank l, a warp sum per 16-bit half
         const uint32_t warp = t >> 5;
-        for (uint32_t row = warp; row < 4 * (RADIX / 2); row += WARPS) {
+        for (uint32_t row = warp; row < 2 * RADIX; row += WARPS) {
             const uint32_t w = lh[(row << 5) + lane];
             uint32_t lo = w & 0xffffu, hi = w >> 16;
 #pragma unroll
@@ -232,9 +237,9 @@ __global__ void __launch_bounds__(BLOCK) count_kernel(CountArgs a) {
                 hi += __shfl_xor_sync(0xffffffffu, hi, o);
             }
             if (lane == 0) {
-                const uint32_t g = row / (RADIX / 2), d = (row % (RADIX / 2)) * 2;
-                sh[g][d] = lo;
-                sh[g][d + 1] = hi;
+                const uint32_t q = row / RADIX, d = row % RADIX;
+                sh[2 * q][d] = lo;
+                sh[2 * q + 1][d] = hi;
             }
         }
         __syncthreads();

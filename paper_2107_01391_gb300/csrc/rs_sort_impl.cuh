@@ -74,12 +74,12 @@ inline uint32_t passes_for(uint32_t cell_bits) {
 inline int count_grid(size_t n, int sms, int per_sm = 8) {
     // at least 64 keys per thread, at most per_sm CTAs per SM (8 measured
     // best at 2^28 keys, 3 resident at a time with 64 KB of lane counters),
-    // and at most 2^21 keys per CTA so that the 16-bit lane counters of
-    // count_kernel (32 lanes x 65535) cannot overflow
+    // and at most 2^20 keys per CTA: a lane's 16-bit counter collects the
+    // keys of its lane in all 8 warps, at most 2^20 / 32 = 32768 of them
     const size_t per_cta = (size_t)BLOCK * 64;
     size_t g = (n + per_cta - 1) / per_cta;
     g = std::min<size_t>(g, (size_t)sms * per_sm);
-    g = std::max<size_t>(g, (n + (1u << 21) - 1) >> 21);
+    g = std::max<size_t>(g, (n + (1u << 20) - 1) >> 20);
     return (int)std::max<size_t>(g, 1);
 }
 
