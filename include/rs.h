@@ -111,7 +111,8 @@ rs_status rs_ctx_status(rs_ctx* ctx, int synchronize);
  * below RS_FILL_CELLS the whole key space is one count array and the output
  * is rebuilt from the counted cells (Eq. 16) without re-reading the keys;
  * otherwise the key's 8-bit digit groups are the dimensions, sorted as
- * buckets from the least significant group on. */
+ * buckets from the least significant group on.  At most 4096 keys are sorted
+ * by one CTA in one launch (every sort call shares this path). */
 #define RS_FILL_CELLS 4096u
 rs_status rs_sort_u32(rs_ctx* ctx, const uint32_t* keys_in, uint32_t* keys_out, size_t n,
                       void* temp, size_t* temp_bytes, rs_stream_t stream);

@@ -14,6 +14,7 @@
 
 #include "rs_ctx.hpp"
 #include "rs_kernels.cuh"
+#include "rs_tile.cuh"
 
 #ifndef RS_PASS_BLOCK
 #define RS_PASS_BLOCK 256
@@ -117,6 +118,39 @@ rs_status run_sort(rs_ctx* ctx, const void* keys_in, void* keys_out, const void*
 
     DeviceGuard dg(ctx->device);
     if (!dg.ok) return RS_ERR_CUDA;
+
+    if (n <= SMALL_TILE) {
+        // one tile: one CTA sorts it on chip in a single launch (the
+        // workspace is not touched)
+        const size_t smem = SMALL_TILE * (sizeof(Cell) + (kPairs ? sizeof(V) : 0));
+        static std::atomic<bool> small_set[64];  // zero-initialised: false
+        if (ctx->device < 64 && !small_set[ctx->device].load(std::memory_order_acquire)) {
+            if (cudaFuncSetAttribute(small_sort_kernel<C, V>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem) != cudaSuccess)
+                return RS_ERR_CUDA;
+            small_set[ctx->device].store(true, std::memory_order_release);
+        }
+        SmallArgs sa{};
+        sa.keys_in = keys_in;
+        sa.keys_out = keys_out;
+        sa.vals_in = vals_in;
+        sa.vals_out = vals_out;
+        sa.n = (uint32_t)n;
+        sa.passes = passes;
+        sa.prm = prm;
+        sa.status = ctx->d_status;
+        sa.info = static_cast<DevInfo*>(ctx->d_info);
+        sa.skip = skip;
+        {
+            LaunchTimer lt(ctx, KC_PASS, stream);
+            small_sort_kernel<C, V><<<1, BLOCK, smem, stream>>>(sa);
+        }
+        ctx->last_passes_total = passes;
+        ctx->last_tiles = 1;
+        return cudaGetLastError() == cudaSuccess ? RS_OK : RS_ERR_CUDA;
+    }
+
     unsigned char* T = static_cast<unsigned char*>(temp);
     DevPlan* plan = reinterpret_cast<DevPlan*>(T + L.plan);
     uint32_t* hist = reinterpret_cast<uint32_t*>(T + L.hist);

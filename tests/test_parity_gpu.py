@@ -142,6 +142,65 @@ def test_tile_boundaries(rs, ctx, oracle, shape, where):
     assert ctx.last_plan()["tiles"] == -(-n // T)
 
 
+@pytest.mark.parametrize("n", [1, 2, 33, 1000, 4095, 4096])
+@pytest.mark.parametrize("kind", ["u32_pairs", "u64_pairs", "u32_u64v_in_place", "dec_keys",
+                                  "narrow_keys"])
+def test_single_tile_sorts(rs, ctx, oracle, kind, n):
+    # at most 4096 keys: one CTA sorts the whole input on chip in one launch
+    rng = np.random.default_rng(n + len(kind))
+    if kind == "u32_pairs":
+        keys = rng.integers(0, 1 << 32, n, dtype=np.uint32)
+        keys[::3] = keys[0]  # ties
+        vals = np.arange(n, dtype=np.uint32)
+        rk, rv, _ = oracle.sort_pairs(keys, vals)
+        ko, vo = rs.rs_sort_pairs(to_dev(keys), to_dev(vals), ctx=ctx)
+        ctx.check()
+        assert np.array_equal(from_dev(ko, np.uint32), rk)
+        assert np.array_equal(from_dev(vo, np.uint32), rv)
+    elif kind == "u64_pairs":
+        keys = W.u64_keys(n, seed_extra=n)
+        keys[1::4] = keys[0]
+        vals = np.arange(n, dtype=np.uint32) * np.uint32(7)
+        rk, rv, _ = oracle.sort_pairs(keys, vals)
+        ko, vo = rs.rs_sort_pairs(to_dev(keys), to_dev(vals), ctx=ctx)
+        ctx.check()
+        assert np.array_equal(from_dev(ko, np.uint64), rk)
+        assert np.array_equal(from_dev(vo, np.uint32), rv)
+    elif kind == "u32_u64v_in_place":
+        keys = rng.integers(0, 50, n, dtype=np.uint32)
+        vals = np.arange(n, dtype=np.uint64) << np.uint64(33)
+        rk, rv, _ = oracle.sort_pairs(keys, vals)
+        dk, dv = to_dev(keys), to_dev(vals)
+        rs.rs_sort_pairs(dk, dv, dk, dv, ctx=ctx)
+        ctx.check()
+        assert np.array_equal(from_dev(dk, np.uint32), rk)
+        assert np.array_equal(from_dev(dv, np.uint64), rv)
+    elif kind == "dec_keys":
+        keys = W.decimals(n, 9, 9, seed_extra=n)  # 64-bit cells, 8 digit groups
+        ref, _, _ = oracle.sort_fixed_decimal(keys, 9, 9)
+        out = rs.rs_sort_fixed_decimal(to_dev(keys), 9, 9, ctx=ctx)
+        ctx.check()
+        assert np.array_equal(from_dev(out, np.int64), ref)
+    else:  # keys in [0, 1000): the upper digit groups are skipped
+        keys = W.digits3(n, seed_extra=n)
+        ref, _, _ = oracle.sort_u32(keys)
+        assert np.array_equal(_sort_u32(rs, ctx, keys), ref)
+        assert ctx.last_plan()["passes_run"] <= 2
+    assert ctx.last_plan()["tiles"] == 1
+
+
+def test_single_tile_boundary(rs, ctx, oracle):
+    # 4096 keys take the single-CTA path (one launch), 4097 the device-wide
+    # one (count, fill, four digit-group passes)
+    for n, launches in ((4096, 1), (4097, 6)):
+        keys = W.u32_keys(n, seed_extra=77)
+        ref, _, _ = oracle.sort_u32(keys)
+        before = ctx.launch_count()
+        assert np.array_equal(_sort_u32(rs, ctx, keys), ref)
+        assert ctx.launch_count() - before == launches
+        assert ctx.last_plan()["mode"] == "passes"
+
+
 # --------------------------------------------------------------- decimals
 
 
