@@ -48,6 +48,19 @@ def test_backward_is_the_reference_scatter(ag, dtype):
     assert torch.equal(gx, ref)
 
 
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_long_rows_forward_and_backward(ag, dtype):
+    # rows longer than the backward's shared-memory row (96 KB), and long
+    # enough for the segmented sort's device tier in the forward
+    x = torch.from_numpy(W.distinct_rows(3, 40_000)).to(dtype).cuda().requires_grad_(True)
+    vals, perm = ag.sort(x)
+    ref = torch.sort(x.detach(), dim=-1, stable=True)
+    assert torch.equal(vals, ref.values) and torch.equal(perm, ref.indices)
+    g = torch.randn_like(vals)
+    (gx,) = torch.autograd.grad(vals, x, g)
+    assert torch.equal(gx, torch.zeros_like(g).scatter_(1, perm, g))
+
+
 def test_fp64_finite_differences(ag):
     x = torch.from_numpy(W.distinct_rows(4, 64).astype(np.float64)).cuda().requires_grad_(True)
     # keys differ by at least 1, so a 1e-6 step never reorders a row
