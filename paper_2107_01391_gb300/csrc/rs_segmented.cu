@@ -723,6 +723,55 @@ rs_status run_segmented(rs_ctx* ctx, const void* keys_in, void* keys_out, const 
     if (num_segs == 0 || n == 0) return RS_OK;
     DeviceGuard dg(ctx->device);
     if (!dg.ok) return RS_ERR_CUDA;
+
+    // equal rows of 64 .. ROW_TILE keys: one CTA per row sorts it on chip in
+    // one read and one write (no size classes, no workspace).  Rows above
+    // SMALL_TILE hold 32 keys per thread, which leaves room for 4-byte
+    // values only; an argsort's indices travel as 32-bit words.
+    const bool narrow_values = !kPairs || sizeof(VS) == 4 || iota;
+    if (!seg_offsets && n / num_segs > WARP_SEG_MAX &&
+        (n / num_segs <= SMALL_TILE || (n / num_segs <= ROW_TILE && narrow_values))) {
+        const uint32_t len = (uint32_t)(n / num_segs);
+        RowsArgs ra{};
+        ra.keys_in = keys_in;
+        ra.keys_out = keys_out;
+        ra.vals_in = vals_in;
+        ra.vals_out = vals_out;
+        ra.rows = num_segs;
+        ra.len = len;
+        ra.iota = iota;
+        ra.passes = passes_for(cell_bits);
+        ra.prm = prm;
+        ra.status = ctx->d_status;
+        const int sms = sm_count(ctx->device);
+        auto launch = [&](auto kern, uint32_t tile, size_t val_bytes) -> rs_status {
+            const size_t smem = tile * (sizeof(Cell) + val_bytes);
+            if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem) != cudaSuccess)
+                return RS_ERR_CUDA;
+            int per_sm = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLOCK, smem) !=
+                    cudaSuccess ||
+                per_sm < 1)
+                per_sm = 1;
+            const int grid = (int)std::min<size_t>((size_t)sms * per_sm, num_segs);
+            LaunchTimer lt(ctx, KC_SEG, st);
+            kern<<<grid, BLOCK, smem, st>>>(ra);
+            return RS_OK;
+        };
+        const size_t vb = kPairs ? sizeof(VS) : 0;
+        rs_status rs_;
+        if (len <= SMALL_TILE) {
+            rs_ = launch(tile_rows_kernel<C, V, SMALL_IPT>, SMALL_TILE, vb);
+        } else {
+            if constexpr (!kPairs || sizeof(VS) == 4)
+                rs_ = launch(tile_rows_kernel<C, V, ROW_IPT>, ROW_TILE, vb);
+            else  // an argsort with 8-byte indices: carried as 32-bit words
+                rs_ = launch(tile_rows_kernel<C, V, ROW_IPT, uint32_t>, ROW_TILE, 4);
+        }
+        if (rs_ != RS_OK) return rs_;
+        return cudaGetLastError() == cudaSuccess ? RS_OK : RS_ERR_CUDA;
+    }
     unsigned char* T = static_cast<unsigned char*>(temp);
     SegControl* ctl = reinterpret_cast<SegControl*>(T + L.ctl);
     uint32_t* order = reinterpret_cast<uint32_t*>(T + L.order);

@@ -122,29 +122,30 @@ rs_status run_sort(rs_ctx* ctx, const void* keys_in, void* keys_out, const void*
     if (n <= SMALL_TILE) {
         // one tile: one CTA sorts it on chip in a single launch (the
         // workspace is not touched)
+        auto kern = tile_rows_kernel<C, V, SMALL_IPT>;
         const size_t smem = SMALL_TILE * (sizeof(Cell) + (kPairs ? sizeof(V) : 0));
         static std::atomic<bool> small_set[64];  // zero-initialised: false
         if (ctx->device < 64 && !small_set[ctx->device].load(std::memory_order_acquire)) {
-            if (cudaFuncSetAttribute(small_sort_kernel<C, V>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+            if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem) != cudaSuccess)
                 return RS_ERR_CUDA;
             small_set[ctx->device].store(true, std::memory_order_release);
         }
-        SmallArgs sa{};
-        sa.keys_in = keys_in;
-        sa.keys_out = keys_out;
-        sa.vals_in = vals_in;
-        sa.vals_out = vals_out;
-        sa.n = (uint32_t)n;
-        sa.passes = passes;
-        sa.prm = prm;
-        sa.status = ctx->d_status;
-        sa.info = static_cast<DevInfo*>(ctx->d_info);
-        sa.skip = skip;
+        RowsArgs ra{};
+        ra.keys_in = keys_in;
+        ra.keys_out = keys_out;
+        ra.vals_in = vals_in;
+        ra.vals_out = vals_out;
+        ra.rows = 1;
+        ra.len = (uint32_t)n;
+        ra.passes = passes;
+        ra.prm = prm;
+        ra.status = ctx->d_status;
+        ra.info = static_cast<DevInfo*>(ctx->d_info);
+        ra.skip = skip;
         {
             LaunchTimer lt(ctx, KC_PASS, stream);
-            small_sort_kernel<C, V><<<1, BLOCK, smem, stream>>>(sa);
+            kern<<<1, BLOCK, smem, stream>>>(ra);
         }
         ctx->last_passes_total = passes;
         ctx->last_tiles = 1;

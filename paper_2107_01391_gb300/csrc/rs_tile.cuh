@@ -83,92 +83,109 @@ __device__ __forceinline__ void rank_scatter(const Cell (&k)[IPT], const VS (&v)
 
 
 // ----------------------------------------------------------------------------
-// A whole sort of at most SMALL_TILE keys in one CTA and one launch: the keys
-// (and values) are loaded once into registers, ranked through shared memory
-// once per non-trivial 8-bit digit group, and written once.  Every input is
-// in registers before the first store, so the sort may be in place.  A group
-// in which every key has the same digit is an identity permutation and is
-// skipped (one block-wide AND).
+// Whole sorts of equal rows of at most BLOCK * IPT keys, one row per CTA at a
+// time (a grid-stride loop over rows): the row's keys (and values) are loaded
+// once into registers, ranked through shared memory once per non-trivial
+// 8-bit digit group, and written once.  Every input is in registers before
+// the first store, so the sort may be in place.  A group in which every key
+// of the row has the same digit is an identity permutation and is skipped
+// (one block-wide AND).  One row of at most SMALL_TILE keys is how every
+// small sort runs; equal segments of up to ROW_TILE keys use the same kernel.
 
 constexpr int SMALL_IPT = 16;
 constexpr uint32_t SMALL_TILE = BLOCK * SMALL_IPT;
+constexpr int ROW_IPT = 32;
+constexpr uint32_t ROW_TILE = BLOCK * ROW_IPT;
 
-struct SmallArgs {
+struct RowsArgs {
     const void* keys_in;
     void* keys_out;
-    const void* vals_in;
+    const void* vals_in;   // NULL with iota: values are the key's index in its row
     void* vals_out;
-    uint32_t n;       // 1 .. SMALL_TILE
-    uint32_t passes;  // digit groups of the cell
+    uint64_t rows;
+    uint32_t len;          // keys per row, 1 .. BLOCK * IPT
+    uint32_t iota;
+    uint32_t passes;       // digit groups of the cell
     CodecParams prm;
     uint32_t* status;
-    DevInfo* info;
-    const uint32_t* skip;  // non-zero at run time: the sort is a no-op
+    DevInfo* info;         // nullable: the plan report of a single sort
+    const uint32_t* skip;  // nullable; non-zero at run time: the sort is a no-op
 };
 
-template <class C, typename V>
-__global__ void __launch_bounds__(BLOCK) small_sort_kernel(SmallArgs a) {
+// VR: the type a value is carried in through the passes (registers and
+// shared memory); V is its type in memory.  An argsort's indices are below
+// BLOCK * IPT, so they travel as 32-bit words whatever their output width.
+template <class C, typename V, int IPT, typename VR = V>
+__global__ void __launch_bounds__(BLOCK, 2) tile_rows_kernel(RowsArgs a) {
     using Cell = typename C::Cell;
     using In = typename C::In;
     using Out = typename C::Out;
     constexpr bool kPairs = ValTraits<V>::kPairs;
-    using VS = typename std::conditional<kPairs, V, uint32_t>::type;
+    constexpr uint32_t TILE = BLOCK * IPT;
+    using VS = typename std::conditional<kPairs, VR, uint32_t>::type;
+    using VM = typename std::conditional<kPairs, V, uint32_t>::type;
     if (a.skip && *a.skip) return;
 
     __shared__ TileShared ts;
     __shared__ Cell s_ref;
     extern __shared__ __align__(16) unsigned char smem_dyn[];
     Cell* s_keys = reinterpret_cast<Cell*>(smem_dyn);
-    VS* s_vals = reinterpret_cast<VS*>(smem_dyn + sizeof(Cell) * SMALL_TILE);
+    VS* s_vals = reinterpret_cast<VS*>(smem_dyn + sizeof(Cell) * TILE);
     const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
-    const uint32_t w0 = warp * 32 * SMALL_IPT + lane;  // warp-striped: input order
-
-    Cell k[SMALL_IPT];
-    VS v[SMALL_IPT];
-    bool ok = true;
-#pragma unroll
-    for (int i = 0; i < SMALL_IPT; i++) {
-        const uint32_t j = w0 + i * 32;
-        k[i] = ~Cell(0);
-        v[i] = VS(0);
-        if (j < a.n) {
-            k[i] = C::decode(static_cast<const In*>(a.keys_in)[j], a.prm, ok);
-            if constexpr (kPairs) v[i] = static_cast<const VS*>(a.vals_in)[j];
-        }
-    }
-    if (!ok) atomicOr(a.status, STATUS_RANGE);
-    if (threadIdx.x == 0) s_ref = k[0];  // input position 0
-    __syncthreads();
-    const Cell ref = s_ref;
+    const uint32_t w0 = warp * 32 * IPT + lane;  // warp-striped: input order
+    const uint32_t n = a.len;
     uint32_t moved = 0;
-    for (uint32_t p = 0; p < a.passes; p++) {
-        const uint32_t shift = p * RADIX_BITS;
-        bool same = true;
+
+    for (uint64_t row = blockIdx.x; row < a.rows; row += gridDim.x) {
+        const uint64_t base = row * n;
+        Cell k[IPT];
+        VS v[IPT];
+        bool ok = true;
 #pragma unroll
-        for (int i = 0; i < SMALL_IPT; i++)
-            if (w0 + i * 32 < a.n) same &= digit_of(k[i], shift) == digit_of(ref, shift);
-        if (__syncthreads_and(same)) continue;  // every key in one cell
-        moved++;
-        rank_scatter<Cell, VS, SMALL_IPT, kPairs>(k, v, a.n, shift, ts, s_keys, s_vals);
-#pragma unroll
-        for (int i = 0; i < SMALL_IPT; i++) {
+        for (int i = 0; i < IPT; i++) {
             const uint32_t j = w0 + i * 32;
-            if (j < a.n) {
-                k[i] = s_keys[j];
-                if constexpr (kPairs) v[i] = s_vals[j];
+            k[i] = ~Cell(0);
+            v[i] = VS(0);
+            if (j < n) {
+                k[i] = C::decode(static_cast<const In*>(a.keys_in)[base + j], a.prm, ok);
+                if constexpr (kPairs)
+                    v[i] = a.iota ? (VS)j : (VS) static_cast<const VM*>(a.vals_in)[base + j];
             }
         }
-        __syncthreads();  // s_keys is rewritten by the next group
-    }
+        if (!ok) atomicOr(a.status, STATUS_RANGE);
+        if (threadIdx.x == 0) s_ref = k[0];  // the row's first key
+        __syncthreads();
+        const Cell ref = s_ref;
+        moved = 0;
+        for (uint32_t p = 0; p < a.passes; p++) {
+            const uint32_t shift = p * RADIX_BITS;
+            bool same = true;
 #pragma unroll
-    for (int i = 0; i < SMALL_IPT; i++) {
-        const uint32_t j = w0 + i * 32;
-        if (j < a.n) {
-            static_cast<Out*>(a.keys_out)[j] = C::encode(k[i], a.prm);
-            if constexpr (kPairs) static_cast<VS*>(a.vals_out)[j] = v[i];
+            for (int i = 0; i < IPT; i++)
+                if (w0 + i * 32 < n) same &= digit_of(k[i], shift) == digit_of(ref, shift);
+            if (__syncthreads_and(same)) continue;  // every key in one cell
+            moved++;
+            rank_scatter<Cell, VS, IPT, kPairs>(k, v, n, shift, ts, s_keys, s_vals);
+#pragma unroll
+            for (int i = 0; i < IPT; i++) {
+                const uint32_t j = w0 + i * 32;
+                if (j < n) {
+                    k[i] = s_keys[j];
+                    if constexpr (kPairs) v[i] = s_vals[j];
+                }
+            }
+            __syncthreads();  // s_keys is rewritten by the next group
+        }
+#pragma unroll
+        for (int i = 0; i < IPT; i++) {
+            const uint32_t j = w0 + i * 32;
+            if (j < n) {
+                static_cast<Out*>(a.keys_out)[base + j] = C::encode(k[i], a.prm);
+                if constexpr (kPairs) static_cast<VM*>(a.vals_out)[base + j] = (VM)v[i];
+            }
         }
     }
-    if (threadIdx.x == 0 && a.info) {
+    if (a.info && blockIdx.x == 0 && threadIdx.x == 0) {
         a.info->mode = MODE_PASSES;
         a.info->passes_run = moved;
     }

@@ -185,6 +185,50 @@ def test_warp_tier_uniform_rows(rs, ctx):
                           want.view(np.uint32))
 
 
+# ---- equal rows of 64 .. 8192 keys: one CTA sorts a row on chip ----
+
+
+@pytest.mark.parametrize("rows,length", [(100, 64), (37, 4096), (9, 4097), (5, 8192)])
+@pytest.mark.parametrize("kind", ["u32_pairs", "u64_u64v", "f32_argsort64", "dec_in_place"])
+def test_equal_rows(rs, ctx, oracle, rows, length, kind):
+    rng = np.random.default_rng(rows * length + len(kind))
+    n = rows * length
+    off = np.arange(0, n + 1, length, dtype=np.uint64)
+    if kind == "u32_pairs":
+        keys = rng.integers(0, 1000, n, dtype=np.uint32)  # ties; upper groups trivial
+        vals = rng.integers(0, 1 << 32, n, dtype=np.uint32)
+        ko, vo = rs.rs_sort_segmented(to_dev(keys), None, to_dev(vals), num_segs=rows, ctx=ctx)
+        ctx.check()
+        ref_k, perm = _oracle_segments(oracle, keys, off, oracle.sort_u32)
+        base = np.repeat(off[:-1].astype(np.int64), length)
+        assert np.array_equal(from_dev(ko, np.uint32), ref_k)
+        assert np.array_equal(from_dev(vo, np.uint32), vals[base + perm])
+    elif kind == "u64_u64v":  # 8-byte values above 4096 keys take the general path
+        keys = W.u64_keys(n, seed_extra=rows)
+        keys[::5] = keys[0]
+        vals = rng.integers(0, 1 << 63, n, dtype=np.uint64)
+        ko, vo = rs.rs_sort_segmented(to_dev(keys), None, to_dev(vals), num_segs=rows, ctx=ctx)
+        ctx.check()
+        ref_k, perm = _oracle_segments(oracle, keys, off, oracle.sort_u64)
+        base = np.repeat(off[:-1].astype(np.int64), length)
+        assert np.array_equal(from_dev(ko, np.uint64), ref_k)
+        assert np.array_equal(from_dev(vo, np.uint64), vals[base + perm])
+    elif kind == "f32_argsort64":
+        x = rng.standard_normal(n).astype(np.float32)
+        x[::7] = np.round(x[::7])
+        ko, idx = rs.rs_sort_segmented(to_dev(x), None, num_segs=rows, argsort=True, ctx=ctx)
+        ctx.check()
+        ref = np.argsort(x.reshape(rows, length), axis=1, kind="stable")
+        assert np.array_equal(idx.cpu().numpy().reshape(rows, length), ref)
+    else:
+        keys = W.decimals(n, 4, 2, seed_extra=rows)
+        dk = to_dev(keys)
+        rs.rs_sort_segmented(dk, None, keys_out=dk, num_segs=rows, decimal=(4, 2), ctx=ctx)
+        ctx.check()
+        ref, _ = _oracle_segments(oracle, keys, off, lambda k: oracle.sort_fixed_decimal(k, 4, 2))
+        assert np.array_equal(from_dev(dk, np.int64), ref)
+
+
 def test_bad_offsets_flagged(rs, ctx):
     keys = to_dev(np.arange(100, dtype=np.uint32)[::-1].copy())
     off = to_dev(np.array([0, 50, 40, 100], np.uint64))
