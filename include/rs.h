@@ -112,7 +112,8 @@ rs_status rs_ctx_status(rs_ctx* ctx, int synchronize);
  * is rebuilt from the counted cells (Eq. 16) without re-reading the keys;
  * otherwise the key's 8-bit digit groups are the dimensions, sorted as
  * buckets from the least significant group on.  At most 4096 keys are sorted
- * by one CTA in one launch (every sort call shares this path). */
+ * by one CTA in one launch, on chip (every sort call shares this path and
+ * leaves the workspace untouched). */
 #define RS_FILL_CELLS 4096u
 rs_status rs_sort_u32(rs_ctx* ctx, const uint32_t* keys_in, uint32_t* keys_out, size_t n,
                       void* temp, size_t* temp_bytes, rs_stream_t stream);
@@ -134,9 +135,10 @@ rs_status rs_sort_fixed_decimal(rs_ctx* ctx, const int64_t* keys_in, int64_t* ke
  * kt selects the key type (params required for RS_KEY_I64_DEC, ignored
  * otherwise); val_bytes is 4 or 8, and vals_in/vals_out are device arrays of
  * n values.  val_bytes == 0 with vals_in == vals_out == NULL sorts the keys
- * alone (the keys-only form for every key type).  Float keys (RS_KEY_F32/F64, not in the paper) are mapped to
- * order-preserving unsigned cells of the same width and written back as
- * rs_key_type describes (-0.0 as +0.0, NaNs last as the quiet NaN). */
+ * alone (the keys-only form for every key type).  Float keys (RS_KEY_F32/F64,
+ * not in the paper) are mapped to order-preserving unsigned cells of the
+ * same width and written back as rs_key_type describes (-0.0 as +0.0, NaNs
+ * last as the quiet NaN). */
 rs_status rs_sort_pairs(rs_ctx* ctx, rs_key_type kt, const void* keys_in, void* keys_out,
                         const void* vals_in, void* vals_out, size_t val_bytes, size_t n,
                         const rs_key_params* params, void* temp, size_t* temp_bytes,
@@ -160,7 +162,8 @@ rs_status rs_sort_strings(rs_ctx* ctx, const uint8_t* chars, const uint32_t* off
                           uint32_t max_len, uint32_t* perm_out, void* temp, size_t* temp_bytes,
                           rs_stream_t stream);
 
-/* Segmented sort: num_segs independent stable sorts in one call.  Segment
+/* Segmented sort: num_segs independent stable sorts in one call (equal
+ * segments of 64..8192 keys: one CTA sorts each row on chip).  Segment
  * s covers positions [seg_offsets[s], seg_offsets[s+1]) of the arrays; every
  * segment is a bucket of its own (§2.2).  Positions outside every segment
  * are left unwritten.
