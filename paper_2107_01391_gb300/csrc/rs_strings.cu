@@ -60,9 +60,10 @@ __global__ void __launch_bounds__(BLOCK) alphabet_kernel(const uint8_t* chars,
     const uint64_t gsize = (uint64_t)gridDim.x * BLOCK;
     bool bad = false;
     uint32_t longest = 0;
+    const uint32_t last = n ? offsets[n] : 0;
     for (uint64_t i = gtid; i < n; i += gsize) {
         const uint32_t b = offsets[i], e = offsets[i + 1];
-        if (e < b || e > offsets[n]) {
+        if (e < b || e > last) {
             bad = true;  // offsets must not decrease nor pass offsets[n]
             continue;
         }
@@ -73,12 +74,24 @@ __global__ void __launch_bounds__(BLOCK) alphabet_kernel(const uint8_t* chars,
         }
         longest = max(longest, len);
     }
-    // bytes that occur: the char buffer between the first and last offset
-    const uint32_t c0 = n ? offsets[0] : 0, c1 = n ? offsets[n] : 0;
-    for (uint64_t c = (uint64_t)c0 + gtid; c < c1; c += gsize) {
-        const uint32_t b = chars[c];
-        if (!s_present[b]) s_present[b] = 1;  // benign race: every writer stores 1
+    // bytes that occur: the char buffer between the first and last offset,
+    // read 16 bytes at a time (every writer stores 1: the races are benign)
+    const uint32_t c0 = n ? offsets[0] : 0, c1 = last;
+    const uint64_t span = c1 > c0 ? c1 - c0 : 0;
+    const uint64_t mis = (16 - (reinterpret_cast<uintptr_t>(chars + c0) & 15)) & 15;
+    const uint64_t head = mis < span ? mis : span;
+    const uint64_t nvec = (span - head) / 16;
+    for (uint64_t c = gtid; c < head; c += gsize) s_present[chars[c0 + c]] = 1;
+    const uint4* vec = reinterpret_cast<const uint4*>(chars + c0 + head);
+    for (uint64_t q = gtid; q < nvec; q += gsize) {
+        const uint4 v = __ldcs(&vec[q]);
+        const uint32_t wd[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+#pragma unroll
+            for (int by = 0; by < 4; by++) s_present[(wd[k] >> (8 * by)) & 0xffu] = 1;
     }
+    for (uint64_t c = head + nvec * 16 + gtid; c < span; c += gsize) s_present[chars[c0 + c]] = 1;
     if (bad) atomicOr(status, STATUS_RANGE);
     atomicMax(&s_longest, longest);
     __syncthreads();
@@ -113,30 +126,47 @@ __global__ void __launch_bounds__(BLOCK) alphabet_kernel(const uint8_t* chars,
 // Cells of chunk c: symbols [c*s, (c+1)*s) of each string, packed most
 // significant first.  The first chunk processed reads strings in input order;
 // later chunks read string perm[j] for output slot j.
+// (grid-stride over output slots, so that a skipped chunk costs one short
+// launch; the byte -> symbol table is staged in shared memory)
 __global__ void __launch_bounds__(BLOCK) pack_kernel(const uint8_t* chars, const uint32_t* offsets,
                                                      uint64_t n, uint32_t max_len, uint32_t c,
                                                      const StrPlan* sp, uint64_t* cells,
                                                      uint32_t* idx) {
     if (sp->skip[c]) return;
-    const uint64_t j = (uint64_t)blockIdx.x * BLOCK + threadIdx.x;
-    if (j >= n) return;
+    __shared__ uint32_t s_sym[RADIX];
+    s_sym[threadIdx.x] = sp->present[threadIdx.x];
+    __syncthreads();
     const bool first = c + 1 == sp->chunks;
-    const uint32_t i = first ? (uint32_t)j : idx[j];
     // stay inside chars[0, offsets[n]) even for malformed offsets (flagged
     // as RS_ERR_RANGE by alphabet_kernel)
     const uint32_t end = offsets[n];
-    const uint32_t b = min(offsets[i], end), e = min(offsets[i + 1], end);
-    const uint32_t len = e < b ? 0u : min(e - b, max_len);
     const uint32_t w = sp->width, s = sp->per_chunk;
     const uint32_t p0 = c * s;
-    uint64_t cell = 0;
-    for (uint32_t q = 0; q < s; q++) {
-        const uint32_t pos = p0 + q;
-        const uint32_t sym = pos < len ? sp->present[chars[b + pos]] : 0u;
-        cell = (cell << w) | sym;
+    for (uint64_t j = (uint64_t)blockIdx.x * BLOCK + threadIdx.x; j < n;
+         j += (uint64_t)gridDim.x * BLOCK) {
+        const uint32_t i = first ? (uint32_t)j : idx[j];
+        const uint32_t b = min(offsets[i], end), e = min(offsets[i + 1], end);
+        const uint32_t len = e < b ? 0u : min(e - b, max_len);
+        const uint8_t* str = chars + b;
+        uint64_t cell = 0;
+        if (s <= 16) {
+            // chunks of at most 16 symbols: independent, unrolled byte loads
+            uint32_t byte[16];
+#pragma unroll
+            for (uint32_t q = 0; q < 16; q++)
+                byte[q] = q < s && p0 + q < len ? __ldg(&str[p0 + q]) : 0u;
+#pragma unroll
+            for (uint32_t q = 0; q < 16; q++)
+                if (q < s) cell = (cell << w) | (p0 + q < len ? s_sym[byte[q]] : 0u);
+        } else {
+            for (uint32_t q = 0; q < s; q++) {
+                const uint32_t pos = p0 + q;
+                cell = (cell << w) | (pos < len ? s_sym[__ldg(&str[pos])] : 0u);
+            }
+        }
+        cells[j] = cell;
+        idx[j] = i;
     }
-    cells[j] = cell;
-    idx[j] = i;
 }
 
 }  // namespace
@@ -191,7 +221,8 @@ extern "C" rs_status rs_sort_strings(rs_ctx* ctx, const uint8_t* chars, const ui
         alphabet_kernel<<<std::max(grid, 1), BLOCK, 0, st>>>(chars, offsets, n, max_len,
                                                             chunks_max, sp, ctx->d_status);
     }
-    const unsigned grid_n = (unsigned)((n + BLOCK - 1) / BLOCK);
+    const unsigned grid_n = (unsigned)std::min<size_t>((n + BLOCK - 1) / BLOCK,
+                                                       (size_t)sm_count(ctx->device) * 8);
     for (int c = (int)chunks_max - 1; c >= 0; c--) {
         {
             LaunchTimer lt(ctx, KC_PACK, st);
