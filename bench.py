@@ -625,6 +625,65 @@ def autograd_leg(steps: int, warmup: int):
             "backward_gbs": 16 * n / (bwd * 1e-3) / 1e9}
 
 
+def library_context(steps: int, warmup: int):
+    """torch.sort(stable=True) -- CUB's radix sort on this GPU -- on inputs of
+    the same shapes, beside the library's own call for the same output, both
+    timed the same way (device time, every launch queued behind a short sleep
+    kernel).  Context only: no part of a measured step.  The outputs of the
+    two are compared element by element (a stable sort has one answer)."""
+    import torch
+    from paper_2107_01391_gb300 import api, workloads as W
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        total = 0.0
+        for _ in range(steps):
+            torch.cuda._sleep(400_000)
+            ev[0].record(stream)
+            fn()
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            total += ev[0].elapsed_time(ev[1])
+        return total / steps
+
+    out = {}
+    rows, cols = 4096, 8192
+    x = torch.from_numpy(W.distinct_rows(rows, cols)).cuda()
+    flat = x.reshape(-1)
+    tv, ti = torch.sort(x, dim=-1, stable=True)
+    rv, ri = api.sort(flat, segments=rows, argsort=True)
+    out["rows"] = {
+        "workload": f"{rows} x {cols} float32 rows: sorted values + int64 index within the row",
+        "torch_sort_ms": timed(lambda: torch.sort(x, dim=-1, stable=True)),
+        "rs_ms": timed(lambda: api.sort(flat, segments=rows, argsort=True)),
+        "identical": bool(torch.equal(tv.reshape(-1), rv) and torch.equal(ti.reshape(-1), ri))}
+    del x, flat, tv, ti, rv, ri
+    n = N_KEYS
+    k = torch.from_numpy(W.u32_keys(n, "uniform").view(np.int32)).cuda()
+    # int32 with the sign bit flipped orders like the u32 keys
+    kf = torch.bitwise_xor(k, torch.tensor(-(1 << 31), dtype=torch.int32, device="cuda"))
+    tv, ti = torch.sort(kf, stable=True)
+    rv, ri = api.sort(k, argsort=True)
+    same = bool(torch.equal(ti, ri) and torch.equal(
+        torch.bitwise_xor(tv, torch.tensor(-(1 << 31), dtype=torch.int32, device="cuda")), rv))
+    del tv, ti, rv, ri
+    out["u32_argsort"] = {
+        "workload": "2^28 uniform u32 keys: sorted keys + int64 input index (stable argsort); "
+                    "torch sorts them as int32 with the sign bit flipped",
+        "torch_sort_ms": timed(lambda: torch.sort(kf, stable=True)),
+        "rs_ms": timed(lambda: api.sort(k, argsort=True)),
+        "identical": same}
+    del k, kf
+    torch.cuda.empty_cache()
+    for v in out.values():
+        v["speedup"] = v["torch_sort_ms"] / v["rs_ms"]
+    return out
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -806,6 +865,8 @@ def run_ours(args):
     if not args.no_configs and world == 1:
         cfgs = configs_leg(binding, ctx, max(3, min(args.steps, 10)), max(3, min(args.warmup, 3)),
                            hbm_peak)
+        cfgs["library_context"] = library_context(max(3, min(args.steps, 10)),
+                                                  max(3, min(args.warmup, 3)))
 
     if rank != 0:
         if world > 1:

@@ -15,17 +15,22 @@
 //          registers and sorted entirely on chip: one rank-and-scatter
 //          through shared memory per 8-bit digit group, then one coalesced
 //          write (16 bytes per u32 key+value pair in total);
-//        - every longer segment is first read once to count all its digit
-//          groups; a segment below 2^DEV_MIN_LOG2 keys is then sorted by its
-//          CTA alone: per non-trivial group a sweep over its tiles in input
-//          order with running cell offsets in shared memory (a
-//          CTA-sequential extraction cycle, no look-back);
+//        - a longer segment below 2^DEV_MIN_LOG2 keys is first read once
+//          to count all its digit groups, then sorted by its CTA alone: per
+//          non-trivial group a sweep over its tiles in input order with
+//          running cell offsets in shared memory (a CTA-sequential
+//          extraction cycle, no look-back);
 //        - a segment of 2^DEV_MIN_LOG2 keys or more (these come first in the
-//          list) leaves its groups' raster-order starts and the set of
-//          non-trivial groups in global memory for the device tier;
+//          list) is counted the same way (or, when longer than one CTA's
+//          share of the batch, tile-parallel by step 5); its groups'
+//          raster-order starts and the set of non-trivial groups are left in
+//          global memory for the device tier;
 //   4. seg_tiles_kernel  (before 3) gives every device-tier segment a
 //                        contiguous range of device tiles;
-//   5. seg_pass_kernel   the device tier, once per digit group: all the
+//   5. seg_count_kernel  (before 3) counts every digit group of the device
+//                        tier's longest segments, one tile per CTA step
+//                        (the others are counted by the CTA that takes them);
+//   6. seg_pass_kernel   the device tier, once per digit group: all the
 //                        tiles of all device-tier segments in one launch,
 //                        each ranked like the device-wide pass and placed
 //                        with a decoupled look-back that stops at its
@@ -65,6 +70,7 @@ struct SegControl {
     uint32_t n_large;                  // segments of the device tier (a prefix of the order)
     uint32_t dev_tiles;                // device tiles handed out
     uint32_t dev_counter[MAX_PASSES];  // tile claims of each device-tier pass
+    uint32_t long_tiles;               // device tiles of segments counted tile-parallel
 };
 
 struct SegArgs {
@@ -90,10 +96,14 @@ struct SegArgs {
     uint32_t* dev_use;     // [n_large] bit p: digit group p moves data
     uint32_t* tile_start;  // [n_large] first device tile of the segment
     uint32_t* tile_owner;  // [max_tiles] order index of the segment owning a tile
+    uint32_t* long_tile;   // [max_tiles] the device tiles of segments of count_par_min keys or more
     uint32_t* lookback[2];
     uint64_t max_tiles;
     uint32_t n_large_max;  // room of bins, dev_use and tile_start
     uint32_t dev_tile;     // keys per device tile
+    // device-tier segments of at least this many keys are counted tile by
+    // tile by seg_count_kernel; shorter ones by the CTA that takes them
+    uint64_t count_par_min;
 };
 
 // Size class: 0 holds the largest segments (2^63 and up), 63 the empty ones.
@@ -173,7 +183,70 @@ __global__ void __launch_bounds__(BLOCK) seg_tiles_kernel(SegArgs a) {
         }
         a.tile_start[i] = start;
         for (uint32_t j = 0; j < tiles; j++) a.tile_owner[start + j] = (uint32_t)i;
+        // a long segment's tiles are listed for seg_count_kernel, which adds
+        // their counts into the segment's rows of bins: they start at zero
+        if (hi - lo >= a.count_par_min) {
+            const uint32_t ls = atomicAdd(&a.ctl->long_tiles, tiles);  // <= dev_tiles
+            for (uint32_t j = 0; j < tiles; j++) a.long_tile[ls + j] = start + j;
+            for (uint32_t w = 0; w < a.passes * RADIX; w++)
+                a.bins[(uint64_t)i * a.passes * RADIX + w] = 0;
+        }
     }
+}
+
+// The hashing cycle (§3.1) of the device tier's longest segments (those of
+// at least count_par_min keys), one device tile per CTA step (a persistent
+// grid): the tile's keys are counted for every digit group in shared memory
+// and the non-zero counts are added into the owning segment's rows of bins,
+// so such a segment is counted by as many CTAs as it has tiles, not by the
+// one CTA of seg_sort_kernel that takes it.  That CTA then turns the counts
+// into raster-order starts.
+template <class C>
+__global__ void __launch_bounds__(BLOCK) seg_count_kernel(SegArgs a) {
+    using Cell = typename C::Cell;
+    using In = typename C::In;
+    __shared__ uint32_t sh[MAX_PASSES][RADIX];
+    const uint32_t t = threadIdx.x;
+    const uint32_t n_large = __ldcg(&a.ctl->n_large);
+    const uint32_t dev_tiles = (uint32_t)min((uint64_t)__ldcg(&a.ctl->dev_tiles), a.max_tiles);
+    const uint32_t long_tiles = min(__ldcg(&a.ctl->long_tiles), dev_tiles);
+    const uint32_t words = a.passes * RADIX;
+    const In* kin = static_cast<const In*>(a.keys_in);
+    bool ok = true;
+    for (uint32_t k = blockIdx.x; k < long_tiles; k += gridDim.x) {
+        const uint32_t g = a.long_tile[k];
+        if (g >= dev_tiles) continue;  // cannot happen: written by seg_tiles_kernel
+        // the owner, checked as seg_pass_kernel checks it (uniform per CTA)
+        const uint32_t slot = a.tile_owner[g];
+        uint64_t lo = 0, hi = 0;
+        uint32_t first_tile = 0;
+        bool own = slot < n_large;
+        if (own) {
+            first_tile = a.tile_start[slot];
+            own = seg_bounds(a, a.order[slot], lo, hi) && first_tile != 0xffffffffu &&
+                  g >= first_tile && (uint64_t)(g - first_tile) * a.dev_tile < hi - lo &&
+                  hi - lo >= a.count_par_min;
+        }
+        if (!own) continue;
+        for (uint32_t i = t; i < words; i += BLOCK) (&sh[0][0])[i] = 0;
+        __syncthreads();
+        const uint64_t base = lo + (uint64_t)(g - first_tile) * a.dev_tile;
+        const uint64_t end = min(hi, base + a.dev_tile);
+        for (uint64_t j = base + t; j < end; j += BLOCK) {
+            const Cell c = C::decode(kin[j], a.prm, ok);
+#pragma unroll
+            for (uint32_t p = 0; p < sizeof(Cell); p++)
+                if (p < a.passes) atomicAdd(&sh[p][digit_of(c, p * RADIX_BITS)], 1u);
+        }
+        __syncthreads();
+        uint32_t* row = a.bins + (uint64_t)slot * words;
+        for (uint32_t i = t; i < words; i += BLOCK) {
+            const uint32_t v = (&sh[0][0])[i];
+            if (v) atomicAdd(&row[i], v);
+        }
+        __syncthreads();  // sh is cleared for the next tile
+    }
+    if (!ok) atomicOr(a.status, STATUS_RANGE);
 }
 
 __global__ void __launch_bounds__(BLOCK) seg_order_kernel(SegArgs a, uint32_t* order) {
@@ -353,10 +426,15 @@ __global__ void __launch_bounds__(BLOCK, seg_ctas_per_sm<C, V>()) seg_sort_kerne
             continue;
         }
 
-        // ---- above one tile: count every digit group in one read ----
-        for (uint32_t i = t; i < MAX_PASSES * RADIX; i += BLOCK) (&s_hist[0][0])[i] = 0;
-        __syncthreads();
-        {
+        // ---- above one tile: count every digit group in one read (the
+        // device tier's longest segments were counted tile by tile by
+        // seg_count_kernel) ----
+        if (device_tier && len >= a.count_par_min) {
+            const uint32_t* row = a.bins + (uint64_t)first_w * a.passes * RADIX;
+            for (uint32_t i = t; i < a.passes * RADIX; i += BLOCK) (&s_hist[0][0])[i] = row[i];
+        } else {
+            for (uint32_t i = t; i < MAX_PASSES * RADIX; i += BLOCK) (&s_hist[0][0])[i] = 0;
+            __syncthreads();
             bool ok = true;
             const In* kin = static_cast<const In*>(a.keys_in);
             for (uint64_t j = lo + t; j < hi; j += BLOCK) {
@@ -668,11 +746,11 @@ __global__ void __launch_bounds__(BLOCK, 2) seg_pass_kernel(SegArgs a, uint32_t 
 // Workspace of one segmented call.  The device tier needs, per possible
 // large segment (at most n / SEG_TILE of them), the group starts and the
 // moving-group mask, and per possible device tile (a large segment of len
-// keys has ceil(len / dev_tile) <= len / dev_tile + 1 of them) an owner and
-// two look-back rows.
+// keys has ceil(len / dev_tile) <= len / dev_tile + 1 of them) an owner, an
+// entry of the list of tiles counted tile-parallel, and two look-back rows.
 struct SegLayout {
-    size_t ctl, order, keys_tmp, vals_tmp, bins, dev_use, tile_start, tile_owner, lookback0,
-        lookback1, total;
+    size_t ctl, order, keys_tmp, vals_tmp, bins, dev_use, tile_start, tile_owner, long_tile,
+        lookback0, lookback1, total;
     size_t n_large_max, max_tiles;
 };
 
@@ -694,6 +772,7 @@ inline SegLayout seg_layout(size_t n, size_t num_segs, bool equal_segments, size
     L.dev_use = at;     at += align_up(sizeof(uint32_t) * L.n_large_max);
     L.tile_start = at;  at += align_up(sizeof(uint32_t) * L.n_large_max);
     L.tile_owner = at;  at += align_up(sizeof(uint32_t) * L.max_tiles);
+    L.long_tile = at;   at += align_up(sizeof(uint32_t) * L.max_tiles);
     L.lookback0 = at;   at += align_up(sizeof(uint32_t) * RADIX * L.max_tiles);
     L.lookback1 = at;   at += align_up(sizeof(uint32_t) * RADIX * L.max_tiles);
     L.total = at;
@@ -806,26 +885,13 @@ rs_status run_segmented(rs_ctx* ctx, const void* keys_in, void* keys_out, const 
     a.dev_use = reinterpret_cast<uint32_t*>(T + L.dev_use);
     a.tile_start = reinterpret_cast<uint32_t*>(T + L.tile_start);
     a.tile_owner = reinterpret_cast<uint32_t*>(T + L.tile_owner);
+    a.long_tile = reinterpret_cast<uint32_t*>(T + L.long_tile);
     a.lookback[0] = reinterpret_cast<uint32_t*>(T + L.lookback0);
     a.lookback[1] = reinterpret_cast<uint32_t*>(T + L.lookback1);
     a.max_tiles = L.max_tiles;
     a.n_large_max = (uint32_t)L.n_large_max;
     a.dev_tile = DTILE;
     const int sms = sm_count(ctx->device);
-    const int grid_s = (int)std::max<size_t>(1, std::min<size_t>((num_segs + BLOCK - 1) / BLOCK,
-                                                                 (size_t)sms * 4));
-    {
-        LaunchTimer lt(ctx, KC_SEG, st);
-        seg_size_kernel<<<grid_s, BLOCK, 0, st>>>(a);
-    }
-    {
-        LaunchTimer lt(ctx, KC_SEG, st);
-        seg_order_kernel<<<grid_s, BLOCK, 0, st>>>(a, order);
-    }
-    if (L.n_large_max) {
-        LaunchTimer lt(ctx, KC_SEG, st);
-        seg_tiles_kernel<<<grid_s, BLOCK, 0, st>>>(a);
-    }
     const size_t smem = sizeof(Cell) * SEG_TILE + (kPairs ? sizeof(VS) * SEG_TILE : 0);
     auto kern = seg_sort_kernel<C, V>;
     static std::atomic<bool> smem_set[64];  // zero-initialised: false
@@ -840,6 +906,35 @@ rs_status run_segmented(rs_ctx* ctx, const void* keys_in, void* keys_out, const 
         per_sm < 1)
         per_sm = 1;
     const int grid = (int)std::min<size_t>((size_t)sms * per_sm, num_segs);
+    // A segment longer than one CTA's share of the batch would keep its CTA
+    // counting after the others are done: such segments (and only those, so
+    // that a batch of many long segments still overlaps their counting with
+    // the on-chip sorts) are counted tile-parallel.
+    a.count_par_min = std::max<uint64_t>(4ull * DTILE, (n + (size_t)grid - 1) / (size_t)grid);
+    const int grid_s = (int)std::max<size_t>(1, std::min<size_t>((num_segs + BLOCK - 1) / BLOCK,
+                                                                 (size_t)sms * 4));
+    {
+        LaunchTimer lt(ctx, KC_SEG, st);
+        seg_size_kernel<<<grid_s, BLOCK, 0, st>>>(a);
+    }
+    {
+        LaunchTimer lt(ctx, KC_SEG, st);
+        seg_order_kernel<<<grid_s, BLOCK, 0, st>>>(a, order);
+    }
+    if (L.n_large_max) {
+        {
+            LaunchTimer lt(ctx, KC_SEG, st);
+            seg_tiles_kernel<<<grid_s, BLOCK, 0, st>>>(a);
+        }
+        // the longest segments' counts, tile-parallel (with equal segments
+        // the host knows whether there are any)
+        if (seg_offsets || n / num_segs >= a.count_par_min) {
+            const int grid_c =
+                (int)std::max<size_t>(1, std::min<size_t>(L.max_tiles, (size_t)sms * 4));
+            LaunchTimer lt(ctx, KC_SEG, st);
+            seg_count_kernel<C><<<grid_c, BLOCK, 0, st>>>(a);
+        }
+    }
     {
         LaunchTimer lt(ctx, KC_SEG, st);
         kern<<<grid, BLOCK, smem, st>>>(a);

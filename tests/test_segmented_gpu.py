@@ -79,6 +79,40 @@ def test_argsort_mode(rs, ctx, oracle, index_dtype):
     assert np.array_equal(idx.cpu().numpy().astype(np.int64), perm)
 
 
+def test_long_segments_many_device_tiles(rs, ctx, oracle):
+    # segments of hundreds of device tiles: each is counted by many CTAs
+    off = _offsets([3, (1 << 22) + 123, 70_000, (1 << 21) + 5, 1])
+    n = int(off[-1])
+    rng = np.random.default_rng(7)
+    keys = rng.integers(0, 1 << 32, n, dtype=np.uint32)
+    keys[100_000:300_000] = keys[100_000]  # a long run of ties inside the long segment
+    ref_k, perm = _oracle_segments(oracle, keys, off, oracle.sort_u32)
+    ko, idx = rs.rs_sort_segmented(to_dev(keys), to_dev(off), argsort=True, ctx=ctx)
+    ctx.check()
+    assert np.array_equal(from_dev(ko, np.uint32), ref_k)
+    assert np.array_equal(idx.cpu().numpy(), perm)
+
+
+def test_one_segment_argsort(rs, ctx, oracle):
+    # the whole array one segment: the argsort form of a single sort
+    n = (1 << 23) + 77
+    keys = W.u32_keys(n)
+    ref_k, perm, _ = oracle.sort_u32(keys)
+    ko, idx = rs.rs_sort_segmented(to_dev(keys), None, num_segs=1, argsort=True, ctx=ctx)
+    ctx.check()
+    assert np.array_equal(from_dev(ko, np.uint32), ref_k)
+    assert np.array_equal(idx.cpu().numpy(), perm.astype(np.int64))
+
+
+def test_device_tier_range_error_flagged(rs, ctx):
+    # a decimal key beyond its declared digits inside a device-tier segment
+    off = _offsets([10, 40_000, 5])
+    dec = W.decimals(int(off[-1]), 6, 3)
+    dec[20_000] = 10 ** 9  # needs ten digits
+    rs.rs_sort_segmented(to_dev(dec), to_dev(off), decimal=(6, 3), ctx=ctx)
+    assert ctx.status(True) == rs.RS_ERR_RANGE
+
+
 def test_argsort_in_place_all_equal(rs, ctx):
     keys = np.full(3 * 9000, 7, np.uint32)
     dk = to_dev(keys)
