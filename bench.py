@@ -678,6 +678,20 @@ def library_context(steps: int, warmup: int):
         "rs_ms": timed(lambda: api.sort(k, argsort=True)),
         "identical": same}
     del k, kf
+    # fixed-point decimals: the bounded count space (6 + 3 digits and a sign,
+    # 31-bit cells, four digit groups) against a full 64-bit integer sort
+    n3 = 1 << 26
+    dec = torch.from_numpy(W.decimals(n3, 6, 3)).cuda()
+    tv, ti = torch.sort(dec, stable=True)
+    rv, ri = api.sort(dec, decimal=(6, 3), argsort=True)
+    same = bool(torch.equal(tv, rv) and torch.equal(ti, ri))
+    del tv, ti, rv, ri
+    out["decimal_argsort"] = {
+        "workload": "2^26 int64 decimals, 6 + 3 digits, signed: sorted keys + int64 input index",
+        "torch_sort_ms": timed(lambda: torch.sort(dec, stable=True)),
+        "rs_ms": timed(lambda: api.sort(dec, decimal=(6, 3), argsort=True)),
+        "identical": same}
+    del dec
     torch.cuda.empty_cache()
     for v in out.values():
         v["speedup"] = v["torch_sort_ms"] / v["rs_ms"]
