@@ -75,7 +75,8 @@ __global__ void __launch_bounds__(BLOCK) alphabet_kernel(const uint8_t* chars,
         longest = max(longest, len);
     }
     // bytes that occur: the char buffer between the first and last offset,
-    // read 16 bytes at a time (every writer stores 1: the races are benign)
+    // read 16 bytes at a time, four loads in flight per thread (every writer
+    // stores 1: the races are benign)
     const uint32_t c0 = n ? offsets[0] : 0, c1 = last;
     const uint64_t span = c1 > c0 ? c1 - c0 : 0;
     const uint64_t mis = (16 - (reinterpret_cast<uintptr_t>(chars + c0) & 15)) & 15;
@@ -83,14 +84,22 @@ __global__ void __launch_bounds__(BLOCK) alphabet_kernel(const uint8_t* chars,
     const uint64_t nvec = (span - head) / 16;
     for (uint64_t c = gtid; c < head; c += gsize) s_present[chars[c0 + c]] = 1;
     const uint4* vec = reinterpret_cast<const uint4*>(chars + c0 + head);
-    for (uint64_t q = gtid; q < nvec; q += gsize) {
-        const uint4 v = __ldcs(&vec[q]);
+    auto mark = [&](const uint4& v) {
         const uint32_t wd[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
         for (int k = 0; k < 4; k++)
 #pragma unroll
             for (int by = 0; by < 4; by++) s_present[(wd[k] >> (8 * by)) & 0xffu] = 1;
+    };
+    uint64_t q = gtid;
+    for (; q + 3 * gsize < nvec; q += 4 * gsize) {
+        uint4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) v[u] = __ldcs(&vec[q + u * gsize]);
+#pragma unroll
+        for (int u = 0; u < 4; u++) mark(v[u]);
     }
+    for (; q < nvec; q += gsize) mark(__ldcs(&vec[q]));
     for (uint64_t c = head + nvec * 16 + gtid; c < span; c += gsize) s_present[chars[c0 + c]] = 1;
     if (bad) atomicOr(status, STATUS_RANGE);
     atomicMax(&s_longest, longest);
@@ -216,7 +225,7 @@ extern "C" rs_status rs_sort_strings(rs_ctx* ctx, const uint8_t* chars, const ui
     if (cudaMemsetAsync(T, 0, plan_bytes, st) != cudaSuccess) return RS_ERR_CUDA;
     {
         const int grid = (int)std::min<size_t>((n + BLOCK * 8 - 1) / (BLOCK * 8),
-                                               (size_t)sm_count(ctx->device) * 4);
+                                               (size_t)sm_count(ctx->device) * 8);
         LaunchTimer lt(ctx, KC_PACK, st);
         alphabet_kernel<<<std::max(grid, 1), BLOCK, 0, st>>>(chars, offsets, n, max_len,
                                                             chunks_max, sp, ctx->d_status);
