@@ -464,13 +464,14 @@ def configs_leg(binding, ctx, steps: int, warmup: int, hbm_peak: float):
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
 
     def timed(fn, reps, flush=None):
-        # device time: a short sleep kernel ahead of the start event lets the
-        # host queue every launch of fn before the device reaches them
+        # device time: a sleep kernel (about 1 ms) ahead of the start event
+        # lets the host queue every launch of fn before the device reaches
+        # them (a string sort is about 35 launches)
         total = 0.0
         for _ in range(reps):
             if flush is not None:
                 flush()
-            torch.cuda._sleep(400_000)
+            torch.cuda._sleep(2_000_000)
             ev[0].record(stream)
             fn()
             ev[1].record(stream)
@@ -642,7 +643,7 @@ def library_context(steps: int, warmup: int):
         torch.cuda.synchronize()
         total = 0.0
         for _ in range(steps):
-            torch.cuda._sleep(400_000)
+            torch.cuda._sleep(2_000_000)
             ev[0].record(stream)
             fn()
             ev[1].record(stream)
