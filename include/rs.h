@@ -185,7 +185,10 @@ rs_status rs_sort_strings(rs_ctx* ctx, const uint8_t* chars, const uint32_t* off
  * one persistent launch: those of at most 63 keys by one warp each, of at
  * most 4096 keys on chip by one CTA in one read and one write, below 2^14
  * keys by one CTA each; longer ones by device-wide passes over all of them
- * at once, one launch per digit group, with a look-back per segment. */
+ * at once, one launch per digit group, with a look-back per segment.  A
+ * segment longer than one CTA's share of the batch (such as the single
+ * segment of an argsort of one array) is counted tile-parallel first, so
+ * one long segment costs about what a device-wide sort of it costs. */
 #define RS_MAX_SEGMENTED_N (1ull << 40)
 #define RS_MAX_SEGMENT_LEN RS_MAX_N
 rs_status rs_sort_segmented(rs_ctx* ctx, rs_key_type kt, const void* keys_in, void* keys_out,
