@@ -224,7 +224,11 @@ extern "C" rs_status rs_sort_strings(rs_ctx* ctx, const uint8_t* chars, const ui
 
     if (cudaMemsetAsync(T, 0, plan_bytes, st) != cudaSuccess) return RS_ERR_CUDA;
     {
-        const int grid = (int)std::min<size_t>((n + BLOCK * 8 - 1) / (BLOCK * 8),
+        // enough CTAs for the strings and for the bytes (at most n * max_len
+        // of them, 16 per load, 8 loads per thread)
+        const size_t by_strings = (n + BLOCK * 8 - 1) / (BLOCK * 8);
+        const size_t by_bytes = (n * (size_t)max_len + BLOCK * 128 - 1) / (BLOCK * 128);
+        const int grid = (int)std::min<size_t>(std::max(by_strings, by_bytes),
                                                (size_t)sm_count(ctx->device) * 8);
         LaunchTimer lt(ctx, KC_PACK, st);
         alphabet_kernel<<<std::max(grid, 1), BLOCK, 0, st>>>(chars, offsets, n, max_len,
