@@ -859,10 +859,36 @@ def run_ours(args):
         ms_e2e = max_over_ranks(e0.elapsed_time(e1) / steps, world)
         got = out_h[(steps - 1) & 1][0][: 1 << 20].to(torch.int64) & 0xFFFFFFFF
         assert bool((got[1:] >= got[:-1]).all()), "end-to-end output not sorted"
+        # the host links of this box, both directions at once, as the
+        # pipeline runs them: bytes per step over the slower direction's
+        # time bounds the end-to-end rate whatever the kernels do
+        link = {}
+        try:
+            c0, c1, c2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            torch.cuda.synchronize()
+            c0.record(s_in)
+            s_out.wait_event(c0)
+            with torch.cuda.stream(s_in):
+                dev[0][0].copy_(hk, non_blocking=True)
+                dev[0][1].copy_(hv, non_blocking=True)
+                c1.record(s_in)
+            with torch.cuda.stream(s_out):
+                out_h[0][0].copy_(dev[1][2], non_blocking=True)
+                out_h[0][1].copy_(dev[1][3], non_blocking=True)
+                c2.record(s_out)
+            torch.cuda.synchronize()
+            h2d_ms, d2h_ms = c0.elapsed_time(c1), c0.elapsed_time(c2)
+            link = {"h2d_gbs": 8 * n / (h2d_ms * 1e-3) / 1e9,
+                    "d2h_gbs": 8 * n / (d2h_ms * 1e-3) / 1e9,
+                    "ceiling_keys_per_s": world * n / (max(h2d_ms, d2h_ms) * 1e-3),
+                    "what": "one step's copies alone, both directions at once"}
+        except RuntimeError as exc:  # context only: never fails the run
+            link = {"error": str(exc)[:200]}
         e2e = {"value": world * n / (ms_e2e * 1e-3), "unit": "keys/s",
                "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n,
                "ms_per_step": ms_e2e, "steps": steps,
-               "pipeline": "3 streams, 2 buffer sets: H2D(i+1) | sort(i) | D2H(i-1)"}
+               "pipeline": "3 streams, 2 buffer sets: H2D(i+1) | sort(i) | D2H(i-1)",
+               "host_links": link}
         del dev, temp
         torch.cuda.empty_cache()
 
