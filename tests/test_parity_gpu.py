@@ -70,9 +70,12 @@ def test_u32_uniform_keys(rs, ctx, oracle, n):
     assert ctx.last_plan()["mode"] == "passes" or n < 3
 
 
-@pytest.mark.parametrize("dist", ["zipf", "presorted"])
+@pytest.mark.parametrize("dist", ["zipf", "presorted", "reversed"])
 def test_u32_skewed_keys(rs, ctx, oracle, dist):
-    keys = W.u32_keys(200_001, dist)
+    if dist == "reversed":  # descending, with runs of ties
+        keys = np.sort(W.u32_keys(200_001, "uniform") >> 12)[::-1].copy()
+    else:
+        keys = W.u32_keys(200_001, dist)
     ref, _, _ = oracle.sort_u32(keys)
     assert np.array_equal(_sort_u32(rs, ctx, keys), ref)
 
