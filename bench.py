@@ -202,6 +202,32 @@ def table1_keys(lo: int, hi: int, cd: int, n: int) -> np.ndarray:
     return rng.integers(lo * 10 ** cd, hi * 10 ** cd, n).astype(np.int64)
 
 
+def host_info() -> dict:
+    """The host the CPU baseline ran on: logical cores and the CPU model."""
+    import platform
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "processor name") and ":" in line:
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if not model:
+        try:
+            r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+            for line in r.stdout.splitlines():
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    return {"nproc": os.cpu_count(), "cpu_model": model or platform.processor() or "unknown",
+            "machine": platform.machine()}
+
+
 def cpu_baseline(sample_n: int, other_workloads: bool = True):
     """The oracle, as it stands, on the first sample_n pairs of the headline
     workload; then, beside each other workload, on a bounded sample of it."""
@@ -216,6 +242,7 @@ def cpu_baseline(sample_n: int, other_workloads: bool = True):
     keys, vals = W.u32_pairs(sample_n, "uniform")
     dt = timed(lambda: oracle.sort_pairs(keys, vals))
     out = {"value": sample_n / dt, "unit": "keys/s", "cores": 1, "kind": "oracle",
+           "host": host_info(),
            "sample": f"first {sample_n} keys (2^{int(np.log2(sample_n))}) of the uniform "
                      f"u32-pairs workload, one oracle call, {dt:.2f} s single-threaded"}
     # a library stable sort on the same sample, for context
@@ -722,6 +749,7 @@ def run_reference(args):
         "config": dict(workload_config(N_KEYS, "uniform", world),
                        step_sample=REFERENCE_STEP_SAMPLE),
         "cpu_baseline": {"value": value, "unit": "keys/s", "cores": 1, "kind": "oracle",
+                         "host": host_info(),
                          "sample": f"each step sorts the first {REFERENCE_STEP_SAMPLE} keys "
                                    "of the workload with the single-threaded oracle"},
         "e2e": {"value": value, "unit": "keys/s", "h2d_bytes_per_step": 0,

@@ -118,7 +118,13 @@ rs_status rs_ctx_status(rs_ctx* ctx, int synchronize);
 rs_status rs_sort_u32(rs_ctx* ctx, const uint32_t* keys_in, uint32_t* keys_out, size_t n,
                       void* temp, size_t* temp_bytes, rs_stream_t stream);
 
-/* Sort n uint64 keys (keys only); same contract as rs_sort_u32. */
+/* Sort n uint64 keys (keys only).  The hashing and extraction cycles
+ * (§3.1-§3.2) with λ = 0 over the 20 base-10 digits of a 64-bit key; the
+ * cell index of a key is the key itself, split on the device into eight 8-bit
+ * digit groups that act as buckets (§2.2) from the least significant on.
+ * Keys below RS_FILL_CELLS are rebuilt from one count array (Eq. 16); at most
+ * 4096 keys are sorted by one CTA on chip.  Arguments, workspace, aliasing
+ * and errors as for rs_sort_u32. */
 rs_status rs_sort_u64(rs_ctx* ctx, const uint64_t* keys_in, uint64_t* keys_out, size_t n,
                       void* temp, size_t* temp_bytes, rs_stream_t stream);
 
@@ -131,8 +137,12 @@ rs_status rs_sort_fixed_decimal(rs_ctx* ctx, const int64_t* keys_in, int64_t* ke
                                 size_t n, int int_digits, int frac_digits, void* temp,
                                 size_t* temp_bytes, rs_stream_t stream);
 
-/* Stable key/value sort: the value at input i travels with key i.
- * kt selects the key type (params required for RS_KEY_I64_DEC, ignored
+/* Stable key/value sort: the value at input i travels with key i.  This is
+ * the counting-sort placement of §2.3 carried through the extraction cycle
+ * (§3.2): every key is placed at its cell's running output position in input
+ * order, and its payload is placed beside it, so ties keep their input order
+ * (Table 2 marks the paper's keys-only extraction unstable; the placement
+ * form is stable).  kt selects the key type (params required for RS_KEY_I64_DEC, ignored
  * otherwise); val_bytes is 4 or 8, and vals_in/vals_out are device arrays of
  * n values.  val_bytes == 0 with vals_in == vals_out == NULL sorts the keys
  * alone (the keys-only form for every key type).  Float keys (RS_KEY_F32/F64,
@@ -166,8 +176,7 @@ rs_status rs_sort_strings(rs_ctx* ctx, const uint8_t* chars, const uint32_t* off
                           uint32_t max_len, uint32_t* perm_out, void* temp, size_t* temp_bytes,
                           rs_stream_t stream);
 
-/* Segmented sort: num_segs independent stable sorts in one call (equal
- * segments of 64..8192 keys: one CTA sorts each row on chip).  Segment
+/* Segmented sort: num_segs independent stable sorts in one call.  Segment
  * s covers positions [seg_offsets[s], seg_offsets[s+1]) of the arrays; every
  * segment is a bucket of its own (§2.2).  Positions outside every segment
  * are left unwritten.
@@ -192,7 +201,10 @@ rs_status rs_sort_strings(rs_ctx* ctx, const uint8_t* chars, const uint32_t* off
  * at once, one launch per digit group, with a look-back per segment.  A
  * segment longer than one CTA's share of the batch (such as the single
  * segment of an argsort of one array) is counted tile-parallel first, so
- * one long segment costs about what a device-wide sort of it costs. */
+ * one long segment costs about what a device-wide sort of it costs.  Equal
+ * segments (seg_offsets NULL) of 64..4096 keys, or of up to 8192 keys with
+ * no values, 4-byte values or an argsort, take a row path instead: one CTA
+ * sorts each whole row on chip in one read and one write. */
 #define RS_MAX_SEGMENTED_N (1ull << 40)
 #define RS_MAX_SEGMENT_LEN RS_MAX_N
 rs_status rs_sort_segmented(rs_ctx* ctx, rs_key_type kt, const void* keys_in, void* keys_out,
@@ -247,8 +259,10 @@ rs_status rs_traverse_maps(rs_ctx* ctx, const int64_t* keys, size_t n, int int_d
  * plugin or a server that owns every device byte through its own pool) has
  * no allocator it may call and no workspace to pass.
  *
- * rs_sort_u32_noalloc sorts n uint32 keys exactly as rs_sort_u32 does (same
- * kernels, same stable result) but needs no context and no workspace: its
+ * rs_sort_u32_noalloc sorts n uint32 keys with the same result as rs_sort_u32
+ * and the same counting, rebuild and digit-group kernels, but needs no
+ * context and no workspace (unlike rs_sort_u32 it takes that multi-launch
+ * path for n <= 4096 too, rather than the single-CTA sort): its
  * workspace is a fixed RS_NOALLOC_SCRATCH_BYTES device array inside the
  * library, which every GPU that loads the library holds until the process
  * exits.  It allocates nothing.

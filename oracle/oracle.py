@@ -163,11 +163,13 @@ def sort_fixed_decimal(keys, int_digits: int, frac_digits: int, cell_cap: int = 
 def sort_float(keys, cell_cap: int = 0, want_keys: bool = True):
     """Stable sort of float32/float64 keys (-0.0 ties +0.0, NaN last).
 
-    float32 keys are widened to float64 first (exact and order-preserving).
+    float32 keys are widened to float64 first (exact and order-preserving;
+    a signalling NaN widens to a quiet NaN, still a NaN).
     Returns (sorted keys in the input dtype, perm, Stats).
     """
     keys = np.asarray(keys)
-    kd = np.ascontiguousarray(keys, dtype=np.float64)
+    with np.errstate(invalid="ignore"):
+        kd = np.ascontiguousarray(keys, dtype=np.float64)
     n = kd.size
     out = np.empty(n, np.float64) if want_keys else None
     perm = np.empty(n, np.uint64)

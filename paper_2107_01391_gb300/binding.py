@@ -182,6 +182,42 @@ def _cuda(t: torch.Tensor, name: str, nbytes: int, dtypes) -> torch.Tensor:
     return t
 
 
+def _out(t: torch.Tensor, like: torch.Tensor, name: str, dtypes=None,
+         numel: int | None = None) -> torch.Tensor:
+    """Check a caller-given output buffer.
+
+    The C ABI takes bare device pointers and cannot see a buffer's length or
+    device, so an output that is too short or on another GPU would turn into
+    out-of-bounds device writes.  It must be a contiguous CUDA tensor on the
+    input's device with exactly ``numel`` elements (default: as many as
+    ``like``) of an allowed dtype (default: ``like``'s element size).
+    """
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if dtypes is not None and t.dtype not in dtypes:
+        raise TypeError(f"{name}: dtype {t.dtype} not in {dtypes}")
+    if dtypes is None and t.element_size() != like.element_size():
+        raise TypeError(f"{name}: {t.element_size()}-byte elements, "
+                        f"{like.element_size()} expected")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    want = like.numel() if numel is None else numel
+    if t.numel() != want:
+        raise ValueError(f"{name} has {t.numel()} elements, {want} expected")
+    if t.device != like.device:
+        raise ValueError(f"{name} is on {t.device}, the input on {like.device}")
+    return t
+
+
+def _context(ctx: "Context | None", t: torch.Tensor) -> "Context":
+    """The given context (which must belong to t's device) or t's default one."""
+    if ctx is None:
+        return default_context(t.device.index)
+    if ctx.device != t.device.index:
+        raise ValueError(f"context of cuda:{ctx.device} used with a tensor on {t.device}")
+    return ctx
+
+
 def _stream(t: torch.Tensor, stream):
     s = torch.cuda.current_stream(t.device) if stream is None else stream
     return ctypes.c_void_p(s.cuda_stream)
@@ -194,6 +230,10 @@ def _ptr(t):
 def _workspace(query, device, temp):
     need = ctypes.c_size_t(0)
     _check(query(None, ctypes.byref(need)), "workspace query")
+    if temp is not None:
+        _cuda(temp, "temp", 1, (torch.uint8,))
+        if temp.device != torch.device(device):
+            raise ValueError(f"temp is on {temp.device}, the input on {device}")
     if temp is None or temp.numel() < need.value:
         temp = torch.empty(max(need.value, 1), dtype=torch.uint8, device=device)
     return temp, ctypes.c_size_t(temp.numel())
@@ -207,8 +247,8 @@ def rs_sort_u32(keys: torch.Tensor, out: torch.Tensor | None = None, *, ctx: Con
                 stream=None, temp: torch.Tensor | None = None) -> torch.Tensor:
     """Stable ascending sort of uint32 keys (int32 tensors are read as their uint32 bits)."""
     _cuda(keys, "keys", 4, U32_DTYPES)
-    out = torch.empty_like(keys) if out is None else _cuda(out, "out", 4, U32_DTYPES)
-    ctx = ctx or default_context(keys.device.index)
+    out = torch.empty_like(keys) if out is None else _out(out, keys, "out", U32_DTYPES)
+    ctx = _context(ctx, keys)
     n, s, L = keys.numel(), _stream(keys, stream), lib()
     temp, tb = _workspace(lambda t, b: L.rs_sort_u32(ctx.handle, _ptr(keys), _ptr(out), n, t, b, s),
                           keys.device, temp)
@@ -221,8 +261,8 @@ def rs_sort_u64(keys: torch.Tensor, out: torch.Tensor | None = None, *, ctx: Con
                 stream=None, temp: torch.Tensor | None = None) -> torch.Tensor:
     """Stable ascending sort of uint64 keys (int64 tensors are read as their uint64 bits)."""
     _cuda(keys, "keys", 8, U64_DTYPES)
-    out = torch.empty_like(keys) if out is None else _cuda(out, "out", 8, U64_DTYPES)
-    ctx = ctx or default_context(keys.device.index)
+    out = torch.empty_like(keys) if out is None else _out(out, keys, "out", U64_DTYPES)
+    ctx = _context(ctx, keys)
     n, s, L = keys.numel(), _stream(keys, stream), lib()
     temp, tb = _workspace(lambda t, b: L.rs_sort_u64(ctx.handle, _ptr(keys), _ptr(out), n, t, b, s),
                           keys.device, temp)
@@ -236,8 +276,8 @@ def rs_sort_fixed_decimal(keys: torch.Tensor, int_digits: int, frac_digits: int,
                           stream=None, temp: torch.Tensor | None = None) -> torch.Tensor:
     """Stable ascending sort of int64 fixed-point decimals scaled by 10^frac_digits."""
     _cuda(keys, "keys", 8, (torch.int64,))
-    out = torch.empty_like(keys) if out is None else _cuda(out, "out", 8, (torch.int64,))
-    ctx = ctx or default_context(keys.device.index)
+    out = torch.empty_like(keys) if out is None else _out(out, keys, "out", (torch.int64,))
+    ctx = _context(ctx, keys)
     n, s, L = keys.numel(), _stream(keys, stream), lib()
     temp, tb = _workspace(
         lambda t, b: L.rs_sort_fixed_decimal(ctx.handle, _ptr(keys), _ptr(out), n, int_digits,
@@ -286,9 +326,12 @@ def rs_sort_pairs(keys: torch.Tensor, values: torch.Tensor | None,
         if vb not in (4, 8):
             raise TypeError("values must be 4 or 8 bytes per element")
         _cuda(values, "values", vb, (values.dtype,))
-        values_out = torch.empty_like(values) if values_out is None else values_out
-    keys_out = torch.empty_like(keys) if keys_out is None else keys_out
-    ctx = ctx or default_context(keys.device.index)
+        if values.device != keys.device:
+            raise ValueError("keys and values must be on the same device")
+        values_out = (torch.empty_like(values) if values_out is None
+                      else _out(values_out, values, "values_out"))
+    keys_out = torch.empty_like(keys) if keys_out is None else _out(keys_out, keys, "keys_out")
+    ctx = _context(ctx, keys)
     prm = KeyParams(*(decimal or (0, 0)))
     pp = ctypes.byref(prm)
     n, s, L = keys.numel(), _stream(keys, stream), lib()
@@ -346,9 +389,11 @@ def rs_sort_strings(chars: torch.Tensor, offsets: torch.Tensor, max_len: int,
     n = offsets.numel() - 1
     if n < 0:
         raise ValueError("offsets needs n+1 entries")
+    if chars.device != offsets.device:
+        raise ValueError("chars and offsets must be on the same device")
     perm_out = (torch.empty(n, dtype=torch.int32, device=offsets.device) if perm_out is None
-                else _cuda(perm_out, "perm_out", 4, U32_DTYPES))
-    ctx = ctx or default_context(offsets.device.index)
+                else _out(perm_out, offsets, "perm_out", U32_DTYPES, numel=n))
+    ctx = _context(ctx, offsets)
     L = lib()
     fn = L.rs_sort_strings
     s = _stream(offsets, stream)
@@ -390,21 +435,28 @@ def rs_sort_segmented(keys: torch.Tensor, seg_offsets: torch.Tensor | None,
     n = keys.numel()
     if seg_offsets is not None:
         _cuda(seg_offsets, "seg_offsets", 8, (torch.int64, torch.uint64))
+        if seg_offsets.device != keys.device:
+            raise ValueError("seg_offsets must be on the keys' device")
         num_segs = seg_offsets.numel() - 1
     elif num_segs is None:
         raise ValueError("give seg_offsets or num_segs")
-    keys_out = torch.empty_like(keys) if keys_out is None else keys_out
+    keys_out = torch.empty_like(keys) if keys_out is None else _out(keys_out, keys, "keys_out")
     if values is not None:
         vb = values.element_size()
         _cuda(values, "values", vb, (values.dtype,))
-        values_out = torch.empty_like(values) if values_out is None else values_out
+        if values.numel() != n or values.device != keys.device:
+            raise ValueError("values must match the keys' length and device")
+        values_out = (torch.empty_like(values) if values_out is None
+                      else _out(values_out, values, "values_out"))
     elif argsort:
         values_out = (torch.empty(keys.shape, dtype=index_dtype, device=keys.device)
-                      if values_out is None else values_out)
+                      if values_out is None
+                      else _out(values_out, keys, "values_out",
+                                (torch.int32, torch.uint32, torch.int64, torch.uint64)))
         vb = values_out.element_size()
     else:
         vb = 0
-    ctx = ctx or default_context(keys.device.index)
+    ctx = _context(ctx, keys)
     L = lib()
     fn = L.rs_sort_segmented
     prm = KeyParams(*(decimal or (0, 0)))
@@ -431,8 +483,10 @@ def rs_scatter_rows(src: torch.Tensor, perm: torch.Tensor, out: torch.Tensor | N
         raise ValueError("src and perm must be 2-D and of the same shape")
     _cuda(src, "src", src.element_size(), (src.dtype,))
     _cuda(perm, "perm", 8, (torch.int64,))
-    out = torch.empty_like(src) if out is None else out
-    ctx = ctx or default_context(src.device.index)
+    if perm.device != src.device:
+        raise ValueError("src and perm must be on the same device")
+    out = torch.empty_like(src) if out is None else _out(out, src, "out")
+    ctx = _context(ctx, src)
     L = lib()
     fn = L.rs_scatter_rows
     _check(fn(ctx.handle, _ptr(src), _ptr(perm), src.shape[0], src.shape[1],
@@ -458,7 +512,7 @@ def rs_traverse_maps(keys: torch.Tensor, int_digits: int, frac_digits: int,
     hmax = torch.empty(rows, dtype=torch.int32, device=dev)
     hmin = torch.empty(rows, 2, dtype=torch.int32, device=dev)
     k = torch.empty(1, dtype=torch.int64, device=dev)
-    ctx = ctx or default_context(dev.index)
+    ctx = _context(ctx, keys)
     L = lib()
     fn = L.rs_traverse_maps
     s = _stream(keys, stream)
@@ -487,10 +541,19 @@ def rs_sort_u32_noalloc(keys: torch.Tensor, out: torch.Tensor | None = None,
     L = lib()
     fn = L.rs_sort_u32_noalloc
     _cuda(keys, "keys", 4, U32_DTYPES)
-    out = torch.empty_like(keys) if out is None else _cuda(out, "out", 4, U32_DTYPES)
+    out = torch.empty_like(keys) if out is None else _out(out, keys, "out", U32_DTYPES)
+    if status is not None:
+        # the kernels OR error bits into this word: it must be a device int32
+        # on the keys' GPU
+        _cuda(status, "status", 4, (torch.int32, torch.uint32))
+        if status.numel() < 1 or status.device != keys.device:
+            raise ValueError("status must be a one-element int32 tensor on the keys' device")
     st = _ptr(status) if status is not None else ctypes.c_void_p(0)
-    _check(fn(_ptr(keys), _ptr(out), keys.numel(), st, _stream(keys, stream)),
-           "rs_sort_u32_noalloc")
+    # the C call runs on the current device: make it the keys' device, whose
+    # stream is passed
+    with torch.cuda.device(keys.device):
+        _check(fn(_ptr(keys), _ptr(out), keys.numel(), st, _stream(keys, stream)),
+               "rs_sort_u32_noalloc")
     return out
 
 

@@ -42,12 +42,28 @@ constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
 unsigned char* g_scratch_addr[kMaxDevices] = {};
 
-// Device address of g_scratch on the current device (set up once).
-rs_status scratch_address(int device, unsigned char** out) {
+using Cu32 = CodecU32;
+constexpr int kIPT = ipt_for<Cu32, NoVal>();
+constexpr int kPB = pass_block<Cu32, NoVal>();
+constexpr size_t kLaneHist = LANE_HIST_WORDS * sizeof(uint32_t);
+
+// Per-device set-up, done once by the first call on a device (with that
+// device current): the device address of g_scratch, and the opt-in of this
+// file's copies of the counting and pass kernels to more than 48 KB of
+// shared memory (static + dynamic).
+rs_status setup_device(int device, unsigned char** out) {
     std::lock_guard<std::mutex> lock(g_setup_mu);
     if (!g_scratch_addr[device]) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || p == nullptr)
+            return RS_ERR_CUDA;
+        using Smem = PassSmem<uint32_t, NoVal, kIPT, kPB>;
+        if (cudaFuncSetAttribute(count_kernel<Cu32, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kLaneHist) != cudaSuccess ||
+            cudaFuncSetAttribute(pass_kernel<Cu32, NoVal, kIPT, kPB>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)Smem::kBytes) != cudaSuccess)
             return RS_ERR_CUDA;
         g_scratch_addr[device] = static_cast<unsigned char*>(p);
     }
@@ -66,9 +82,9 @@ extern "C" rs_status rs_sort_u32_noalloc(const uint32_t* keys_in, uint32_t* keys
     if (reinterpret_cast<uintptr_t>(status) % 4) return RS_ERR_INVALID;
     if (n == 0) return RS_OK;
 
-    using C = CodecU32;
-    constexpr int IPT = ipt_for<C, NoVal>();
-    constexpr int PB = pass_block<C, NoVal>();
+    using C = Cu32;
+    constexpr int IPT = kIPT;
+    constexpr int PB = kPB;
     constexpr int TILE = PB * IPT;
     constexpr uint32_t passes = 4;
     const Layout L = make_layout(n, passes, TILE, sizeof(uint32_t), 0);
@@ -78,7 +94,7 @@ extern "C" rs_status rs_sort_u32_noalloc(const uint32_t* keys_in, uint32_t* keys
     if (cudaGetDevice(&device) != cudaSuccess || device < 0 || device >= kMaxDevices)
         return RS_ERR_CUDA;
     unsigned char* base = nullptr;
-    rs_status s = scratch_address(device, &base);
+    rs_status s = setup_device(device, &base);
     if (s != RS_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
 
@@ -108,11 +124,7 @@ extern "C" rs_status rs_sort_u32_noalloc(const uint32_t* keys_in, uint32_t* keys
     a.fill_offsets = fill_offsets;
     a.status = status_word;
     a.info = info;
-    constexpr size_t lane_hist = LANE_HIST_WORDS * sizeof(uint32_t);
-    if (cudaFuncSetAttribute(count_kernel<C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)lane_hist) != cudaSuccess)
-        return RS_ERR_CUDA;
-    count_kernel<C, true><<<count_grid(n, sm_count(device)), BLOCK, lane_hist, st>>>(a);
+    count_kernel<C, true><<<count_grid(n, sm_count(device)), BLOCK, kLaneHist, st>>>(a);
 
     FillArgs f{};
     f.keys_out = keys_out;
@@ -124,12 +136,6 @@ extern "C" rs_status rs_sort_u32_noalloc(const uint32_t* keys_in, uint32_t* keys
     fill_kernel<C><<<(unsigned)((n + per_cta - 1) / per_cta), BLOCK, 0, st>>>(f);
 
     using Smem = PassSmem<uint32_t, NoVal, IPT, PB>;
-    // this file's copy of the pass kernel needs its own opt-in to more than
-    // 48 KB of shared memory (static + dynamic)
-    if (cudaFuncSetAttribute(pass_kernel<C, NoVal, IPT, PB>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)Smem::kBytes) != cudaSuccess)
-        return RS_ERR_CUDA;
     for (uint32_t p = 0; p < passes; p++) {
         PassArgs pa{};
         pa.keys_in = keys_in;

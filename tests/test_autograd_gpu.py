@@ -39,6 +39,42 @@ def test_forward_matches_torch_sort(ag):
 
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+@pytest.mark.parametrize("cols", [1000, 8192, 20_000])
+def test_forward_signed_zeros_and_nans(ag, oracle, dtype, cols):
+    """Rows holding -0.0, +0.0 and NaNs with payloads and either sign.  The
+    permutation is the oracle's: -0.0 ties with +0.0 (input order kept) and
+    every NaN sorts last, in input order (torch.sort's order for zeros and
+    quiet NaNs).  The values are x gathered through that permutation, except
+    that the library writes every zero as +0.0 and every NaN as the quiet NaN
+    (its cells have the key's own width, so tied keys cannot keep distinct
+    bits)."""
+    rng = np.random.default_rng(cols)
+    x = np.round(rng.standard_normal((6, cols)) * 3).astype(np.float64)
+    x[:, ::7] = -0.0
+    x[:, 3::11] = 0.0
+    bits = np.array([0x7FF8000000000001, 0xFFF8000000000123, 0x7FF0000000000001,
+                     0xFFFFFFFFFFFFFFFF], np.uint64)
+    if dtype == torch.float32:
+        x = x.astype(np.float32)
+        bits = np.array([0x7FC00001, 0xFFC00123, 0x7F800001, 0xFFFFFFFF], np.uint32)
+    nan = bits.view(x.dtype)
+    for r in range(x.shape[0]):
+        x[r, rng.permutation(cols)[:9]] = nan[rng.integers(0, nan.size, 9)]
+    vals, perm = ag.sort(torch.from_numpy(x).cuda())
+    vals, perm = vals.cpu().numpy(), perm.cpu().numpy()
+    ub = np.uint32 if dtype == torch.float32 else np.uint64
+    for r in range(x.shape[0]):
+        _, ref_p, _ = oracle.sort_float(x[r])
+        ref_p = ref_p.astype(np.int64)
+        assert np.array_equal(perm[r], ref_p)
+        want = x[r][ref_p].copy()
+        want[want == 0] = 0.0          # -0.0 written as +0.0
+        want[np.isnan(want)] = np.nan  # every NaN as the quiet NaN
+        assert np.array_equal(vals[r].view(ub), want.view(ub))
+        assert np.isnan(vals[r][-9:]).all()
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
 def test_backward_is_the_reference_scatter(ag, dtype):
     x = torch.from_numpy(W.distinct_rows(32, 3000)).to(dtype).cuda().requires_grad_(True)
     g = torch.randn(32, 3000, dtype=dtype, device="cuda")

@@ -42,6 +42,10 @@ MUTATIONS = {
     "regen_negative_not_undone": ("mag = (POW10[ks->mag_digits] - 1u) - mag;", ""),
     "float_negatives_not_complemented": ("return negative ? 9u - dig : dig;", "return dig;"),
     "float_nan_before_numbers": ("if (is_nan) return 3u;", "if (is_nan) return 0u;"),
+    "emit_u64_wrong_width": ("((uint64_t*)out)[j] = cell;",
+                             "((uint32_t*)out)[j] = (uint32_t)cell;"),
+    "emit_u32_off_by_one": ("((uint32_t*)out)[j] = (uint32_t)cell;",
+                            "((uint32_t*)out)[j] = (uint32_t)cell + (j > 0 && cell > 0);"),
     "bucket_skips_a_dimension": (
         "rc = sort_bucket(ks, items, scratch, bk[i].lo, bk[i].count, next, cell_cap, st);",
         "rc = sort_bucket(ks, items, scratch, bk[i].lo, bk[i].count, next + 1, cell_cap, st);"),
@@ -60,6 +64,7 @@ def _battery(oracle):
         ("brute_str", lambda: pins.test_bruteforce_strings(oracle, 3)),
         ("u32_numpy", lambda: pins.test_u32_vs_numpy_stable(oracle, 1, 2**32, 3000)),
         ("u64_numpy", lambda: pins.test_u64_vs_numpy_stable(oracle, 1)),
+        ("u64_regen", lambda: pins.test_u64_small_keys_regenerated(oracle, 1000)),
         ("dec_numpy", lambda: pins.test_fixed_decimal_vs_numpy_stable(oracle, 1)),
         ("dec_regen", lambda: pins.test_fixed_decimal_regenerates_negatives(oracle)),
         ("str_bytes", lambda: pins.test_strings_vs_python_bytes_order(oracle, 1)),

@@ -224,6 +224,31 @@ def test_u64_vs_numpy_stable(oracle, seed):
     assert (out == keys[ref]).all()
 
 
+@pytest.mark.parametrize("hi", [1, 10, 1000])
+def test_u64_small_keys_regenerated(oracle, hi):
+    """u64 keys whose digit vectors fit one count array are rebuilt from their
+    cells (Eq. 16) rather than copied: the rebuilt keys must equal numpy's
+    stable sort of the input, and the stats must say they were rebuilt."""
+    rng = np.random.default_rng(hi)
+    keys = rng.integers(0, hi, 3000, dtype=np.uint64)
+    keys[:3] = [0, hi - 1, 0]
+    out, perm, st = oracle.sort_u64(keys)
+    ref = np.argsort(keys, kind="stable")
+    assert st.regenerated
+    assert out.dtype == np.uint64
+    assert (perm.astype(np.int64) == ref).all()
+    assert (out == keys[ref]).all()
+
+
+def test_u32_small_keys_regenerated(oracle):
+    """The same for u32 keys of at most three digits (the 10x10x10 space)."""
+    rng = np.random.default_rng(7)
+    keys = rng.integers(0, 1000, 3000, dtype=np.uint64).astype(np.uint32)
+    out, perm, st = oracle.sort_u32(keys)
+    assert st.regenerated
+    assert (out == np.sort(keys, kind="stable")).all()
+
+
 @pytest.mark.parametrize("seed", [1, 2, 3])
 def test_fixed_decimal_vs_numpy_stable(oracle, seed):
     rng = np.random.default_rng(seed)

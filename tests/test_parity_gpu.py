@@ -377,6 +377,27 @@ def test_u32_pairs_maximum_size(rs, ctx, oracle):
     torch.cuda.empty_cache()
 
 
+def test_fixed_decimal_6_3_full_size(rs, ctx, oracle):
+    """2^26 signed decimals with 6 integer and 3 fraction digits (the
+    decimal workload at its full size), keys and the stable permutation,
+    element by element against the oracle."""
+    n = 1 << 26
+    keys = W.decimals(n, 6, 3)
+    ref_k, perm, _ = oracle.sort_fixed_decimal(keys, 6, 3)
+    dk = to_dev(keys)
+    out = rs.rs_sort_fixed_decimal(dk, 6, 3, ctx=ctx)
+    ctx.check()
+    assert np.array_equal(from_dev(out, np.int64), ref_k)
+    del out
+    vals = np.arange(n, dtype=np.uint32)
+    ko, vo = rs.rs_sort_pairs(dk, to_dev(vals), decimal=(6, 3), ctx=ctx)
+    ctx.check()
+    assert np.array_equal(from_dev(ko, np.int64), ref_k)
+    assert np.array_equal(from_dev(vo, np.uint32), perm.astype(np.uint32))
+    del dk, ko, vo
+    torch.cuda.empty_cache()
+
+
 def test_timing_and_launch_count(rs, ctx):
     keys = to_dev(W.u32_keys(1 << 20))
     ctx.set_timing(True)
@@ -409,6 +430,12 @@ def test_float_pairs(rs, ctx, oracle, fdt, n):
     keys = rng.standard_normal(n).astype(fdt)
     keys[::5] = np.round(keys[::5])  # ties, including +0.0 and -0.0
     special = np.array([0.0, -0.0, np.inf, -np.inf, np.nan, -np.nan, 1e-45, -1e-45], fdt)
+    # NaNs that carry a payload, a sign or the signalling bit pattern
+    ub = np.uint32 if fdt == np.float32 else np.uint64
+    nan_bits = ([0x7FC00001, 0xFFC00123, 0x7F800001, 0xFFFFFFFF] if fdt == np.float32 else
+                [0x7FF8000000000001, 0xFFF8000000000123, 0x7FF0000000000001,
+                 0xFFFFFFFFFFFFFFFF])
+    special = np.concatenate([special, np.array(nan_bits, ub).view(fdt)])
     m = min(n, special.size)
     keys[rng.permutation(n)[:m]] = special[:m]
     vals = np.arange(n, dtype=np.uint32)

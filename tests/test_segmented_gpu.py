@@ -138,19 +138,28 @@ def test_u64_and_decimal_keys(rs, ctx, oracle):
     assert np.array_equal(idx.cpu().numpy(), perm)
 
 
-def test_f32_rows_vs_numpy_stable(rs, ctx):
+def _oracle_float_rows(oracle, x):
+    """Per-row stable order from the oracle's float path, and the keys the
+    library writes for it (-0.0 as +0.0, every NaN as the quiet NaN)."""
+    ref = np.stack([oracle.sort_float(r)[1].astype(np.int64) for r in x])
+    want = np.take_along_axis(x, ref, axis=1)
+    want[want == 0] = 0.0
+    want[np.isnan(want)] = np.nan
+    return ref, want
+
+
+def test_f32_rows_against_oracle(rs, ctx, oracle):
     rng = np.random.default_rng(3)
     rows, length = 64, 5000
     x = rng.standard_normal((rows, length)).astype(np.float32)
     x[:, ::7] = np.round(x[:, ::7])  # ties
     x[0, :4] = [0.0, -0.0, np.inf, -np.inf]
+    x[1, :3] = np.array([0x7FC00001, 0xFFC00000, 0x7F800001], np.uint32).view(np.float32)
     ko, idx = rs.rs_sort_segmented(torch.from_numpy(x).cuda().reshape(-1), None,
                                    num_segs=rows, argsort=True, ctx=ctx)
     ctx.check()
-    ref = np.argsort(x, axis=1, kind="stable")
+    ref, want = _oracle_float_rows(oracle, x)
     assert np.array_equal(idx.cpu().numpy().reshape(rows, length), ref)
-    want = np.take_along_axis(x, ref, axis=1)
-    want[want == 0] = 0.0  # -0.0 is written as +0.0
     assert np.array_equal(ko.cpu().numpy().reshape(rows, length).view(np.uint32),
                           want.view(np.uint32))
 
@@ -202,19 +211,18 @@ def test_warp_tier_u64_decimal_and_argsort(rs, ctx, oracle):
     assert np.array_equal(idx.cpu().numpy().astype(np.int64), perm)
 
 
-def test_warp_tier_uniform_rows(rs, ctx):
+def test_warp_tier_uniform_rows(rs, ctx, oracle):
     # equal segments of 50 keys (no offsets array): every row goes to the warp tier
     rng = np.random.default_rng(13)
     rows, length = 4000, 50
     x = rng.standard_normal((rows, length)).astype(np.float32)
-    x[:, ::3] = np.round(x[:, ::3])  # ties
+    x[:, ::3] = np.round(x[:, ::3])  # ties, including -0.0 and +0.0
+    x[7, :2] = np.array([0xFFC00123, 0x7FC00000], np.uint32).view(np.float32)
     ko, idx = rs.rs_sort_segmented(torch.from_numpy(x).cuda().reshape(-1), None,
                                    num_segs=rows, argsort=True, ctx=ctx)
     ctx.check()
-    ref = np.argsort(x, axis=1, kind="stable")
+    ref, want = _oracle_float_rows(oracle, x)
     assert np.array_equal(idx.cpu().numpy().reshape(rows, length), ref)
-    want = np.take_along_axis(x, ref, axis=1)
-    want[want == 0] = 0.0  # -0.0 is written as +0.0
     assert np.array_equal(ko.cpu().numpy().reshape(rows, length).view(np.uint32),
                           want.view(np.uint32))
 

@@ -47,6 +47,16 @@ def test_lowercase_strings(rs, ctx, oracle, n):
     assert np.array_equal(got, ref.astype(np.uint32))
 
 
+def test_strings_full_size(rs, ctx, oracle):
+    """The 2^24-string workload at its full size: the whole permutation
+    against the oracle, element by element."""
+    n = 1 << 24
+    chars, offsets = W.strings(n)
+    ref, _ = oracle.sort_strings(chars, offsets.astype(np.uint64))
+    got = _gpu_perm(rs, ctx, chars, offsets, 16)
+    assert np.array_equal(got, ref.astype(np.uint32))
+
+
 def test_strings_full_size_sampled(rs, ctx, oracle):
     n = 1 << 24
     chars, offsets = W.strings(n)

@@ -40,7 +40,7 @@ def _call_noalloc(rs, keys_dev, out_dev, status_dev):
               keys_dev.numel(), ctypes.c_void_p(status_dev.data_ptr()), stream)
 
 
-def test_noalloc_matches_rs_sort_u32_twice_in_a_row(rs):
+def test_noalloc_matches_rs_sort_u32_twice_in_a_row(rs, oracle):
     ctx = rs.Context(0)
     status = torch.zeros(1, dtype=torch.int32, device="cuda")
     cases = [
@@ -52,12 +52,34 @@ def test_noalloc_matches_rs_sort_u32_twice_in_a_row(rs):
         d = to_dev(keys)
         want = rs.rs_sort_u32(d, ctx=ctx)
         ctx.check()
+        ref, _, _ = oracle.sort_u32(keys)
+        assert np.array_equal(from_dev(want, np.uint32), ref)
         got = torch.empty_like(d)
         assert _call_noalloc(rs, d, got, status) == rs.RS_OK
         torch.cuda.synchronize()
         assert int(status.item()) == 0
-        assert np.array_equal(from_dev(got, np.uint32), from_dev(want, np.uint32))
+        assert np.array_equal(from_dev(got, np.uint32), ref)
     ctx.close()
+
+
+# Small inputs: unlike rs_sort_u32, which sorts at most 4096 keys in one
+# single-CTA launch, the allocation-free call always runs the counting,
+# rebuild and digit-group launches, here over one partial tile (a tile is
+# 48 x 256 = 12288 keys) or just past one.
+@pytest.mark.parametrize("n", [1, 2, 31, 4096, 4097, 12288, 12289])
+@pytest.mark.parametrize("kind", ["uniform", "digits3"])
+def test_noalloc_small_inputs_against_oracle(rs, oracle, n, kind):
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    keys = (W.u32_keys(n, "uniform", seed_extra=n) if kind == "uniform"
+            else W.digits3(n, seed_extra=n))
+    ref, _, _ = oracle.sort_u32(keys)
+    d = to_dev(keys)
+    for _ in range(2):  # a second call must not see what the first left behind
+        got = torch.empty_like(d)
+        assert _call_noalloc(rs, d, got, status) == rs.RS_OK
+        torch.cuda.synchronize()
+        assert int(status.item()) == 0
+        assert np.array_equal(from_dev(got, np.uint32), ref)
 
 
 def test_noalloc_in_place_and_binding(rs):
@@ -67,6 +89,16 @@ def test_noalloc_in_place_and_binding(rs):
     rs.rs_sort_u32_noalloc(d, out=d)
     torch.cuda.synchronize()
     assert np.array_equal(from_dev(d, np.uint32), want)
+
+
+def test_noalloc_binding_checks_buffers(rs):
+    d = to_dev(W.u32_keys(1000, "uniform", seed_extra=9))
+    with pytest.raises(ValueError):
+        rs.rs_sort_u32_noalloc(d, out=torch.empty(999, dtype=torch.int32, device="cuda"))
+    with pytest.raises(TypeError):
+        rs.rs_sort_u32_noalloc(d, status=torch.zeros(1, dtype=torch.int32))  # host memory
+    with pytest.raises(TypeError):
+        rs.rs_sort_u32_noalloc(d, status=torch.zeros(1, dtype=torch.int64, device="cuda"))
 
 
 def test_noalloc_rejects_more_than_its_workspace(rs):
