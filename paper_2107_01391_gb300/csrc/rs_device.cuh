@@ -168,6 +168,13 @@ __device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
     asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Bulk prefetch of [p, p + bytes) into L2 by the copy engine of the SM (TMA),
+// with no destination in shared memory.  p and bytes must be multiples of
+// 16; the call is a hint and completes asynchronously.
+__device__ __forceinline__ void bulk_prefetch_l2(const void* p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // Lanes of the warp holding the same 8-bit digit: one ballot per bit.  Per
 // bit b: p = bit set, sx = all ones when set, bal = lanes with the bit set,
 // and peers &= ~(bal ^ sx) in one lop3 (truth table 0x90 for a & ~(b ^ c)
@@ -198,6 +205,55 @@ __device__ __forceinline__ uint32_t match_digit(uint32_t d) {
     match_bit<6>(d, m);
     match_bit<7>(d, m);
     return m;
+}
+
+// The same peer mask from the same eight ballots, with a lookup in place of
+// the per-lane selects.  The ballots are warp-uniform, so the peer mask of a
+// digit value depends on nothing else: lane l keeps two table entries, T5[l]
+// = the lanes whose digit bits 3..7 equal l and T3[l & 7] = the lanes whose
+// bits 0..2 equal l & 7, each built against the lane's own index bits (the
+// constants sx).  A key's peers are T5[d >> 3] & T3[d & 7], fetched with two
+// shuffles (the second within groups of 8 lanes, which all hold T3).  Per key
+// row: 8 predicate ops, 8 ballots, 8 table ops, a shift and two shuffles, in
+// place of the 8 selects and 8 masks of match_digit.
+struct LaneBits {
+    uint32_t sx[5];  // all ones where bit b of the lane index is set
+};
+
+__device__ __forceinline__ LaneBits lane_bits() {
+    LaneBits L;
+    const uint32_t lane = lane_id();
+#pragma unroll
+    for (int b = 0; b < 5; b++) L.sx[b] = 0u - ((lane >> b) & 1u);
+    return L;
+}
+
+// bal = lanes whose digit has bit B set; m &= ~(bal ^ sx) (lop3 table 0x90)
+template <int B>
+__device__ __forceinline__ void table_bit(uint32_t d, uint32_t sx, uint32_t& m) {
+    asm("{\n\t"
+        ".reg .pred p;\n\t"
+        ".reg .b32 t, bal;\n\t"
+        "and.b32 t, %1, %2;\n\t"
+        "setp.ne.u32 p, t, 0;\n\t"
+        "vote.sync.ballot.b32 bal, p, 0xffffffff;\n\t"
+        "lop3.b32 %0, %0, bal, %3, 0x90;\n\t"
+        "}"
+        : "+r"(m)
+        : "r"(d), "n"(1u << B), "r"(sx));
+}
+
+__device__ __forceinline__ uint32_t match_digit_lut(uint32_t d, const LaneBits& L) {
+    uint32_t t3 = 0xffffffffu, t5 = 0xffffffffu;
+    table_bit<0>(d, L.sx[0], t3);
+    table_bit<1>(d, L.sx[1], t3);
+    table_bit<2>(d, L.sx[2], t3);
+    table_bit<3>(d, L.sx[0], t5);
+    table_bit<4>(d, L.sx[1], t5);
+    table_bit<5>(d, L.sx[2], t5);
+    table_bit<6>(d, L.sx[3], t5);
+    table_bit<7>(d, L.sx[4], t5);
+    return __shfl_sync(0xffffffffu, t5, d >> 3) & __shfl_sync(0xffffffffu, t3, d, 8);
 }
 
 template <typename T>

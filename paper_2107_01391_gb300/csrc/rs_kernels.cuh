@@ -25,6 +25,14 @@ namespace rs {
 // 2 measured best (1.163 ms per pass; 4: 1.168, 8: 1.176)
 constexpr int LOOKBACK_WINDOW = 2;
 
+// Tiles are claimed in input order, so while a CTA works on tile t the tiles
+// claimed over the next part of a residency period are t + 1 .. t + R (R =
+// resident CTAs of the grid).  Each tile starts an L2 prefetch of the keys and
+// values of tile t + PassArgs::prefetch_ahead (the host sets it to a fraction
+// PREFETCH_FRACTION of R), so that tile's loads find its data in L2 instead
+// of waiting on DRAM.  Too far ahead and the lines are evicted before use.
+constexpr float PREFETCH_FRACTION = 0.5f;
+
 struct CountArgs {
     const void* keys_in;
     uint64_t n;
@@ -283,7 +291,13 @@ struct PassArgs {
     uint32_t* lookback_next;      // cleared here for the next pass
     uint32_t* tile_counter;
     uint32_t* status;
+    uint32_t prefetch_ahead;  // tiles; 0: no prefetch
 };
+
+// The prefetch distance for a grid of `resident` co-resident CTAs.
+inline uint32_t prefetch_ahead_for(int resident) {
+    return (uint32_t)((float)resident * PREFETCH_FRACTION);
+}
 
 struct NoVal {};
 
@@ -314,7 +328,18 @@ struct PassShape {
     static constexpr int kIPT = kCell4 ? (!kPairs ? 48 : (kVal8 ? 28 : 40))
                                        : (!kPairs ? 40 : (kVal8 ? 24 : 28));
     static constexpr int kCTAs = (kCell4 && !kPairs) ? 3 : 2;
+    // table match (match_digit_lut) where its five lane constants fit the
+    // register budget without spilling; match_digit elsewhere
+    static constexpr bool kLut = kCell4 && kPairs && !kVal8;
 };
+
+template <bool kLut>
+__device__ __forceinline__ uint32_t peer_mask(uint32_t d, const LaneBits& L) {
+    if constexpr (kLut)
+        return match_digit_lut(d, L);
+    else
+        return match_digit(d);
+}
 
 template <typename Cell, typename V, int IPT, int PB = BLOCK>
 struct PassSmem {
@@ -436,10 +461,15 @@ __global__ void __launch_bounds__(PB, PB == 256 ? PassShape<C, V>::kCTAs
     for (int e = 0; e < ND; e++) a.lookback_next[(uint64_t)blockIdx.x * RADIX + e * PB + t] = 0;
     for (uint32_t d = lane; d < RADIX; d += 32) ws[warp][d] = 0;
 
+    // every plan word this pass reads, loaded together: one round trip that
+    // overlaps the tile claim (the plan was written by an earlier launch)
     const DevPlan* P = a.plan;
-    if (P->mode != MODE_PASSES || !P->active[a.pass]) return;
-    const bool first = P->first_active == a.pass;
-    const bool last = P->last_active == a.pass;
+    const uint32_t p_mode = __ldg(&P->mode), p_active = __ldg(&P->active[a.pass]);
+    const uint32_t p_first = __ldg(&P->first_active), p_last = __ldg(&P->last_active);
+    const uint32_t src = __ldg(&P->src[a.pass]), dst = __ldg(&P->dst[a.pass]);
+    if (p_mode != MODE_PASSES || !p_active) return;
+    const bool first = p_first == a.pass;
+    const bool last = p_last == a.pass;
 
     if (t == 0) s_tile = claimed;
     __syncthreads();
@@ -448,11 +478,24 @@ __global__ void __launch_bounds__(PB, PB == 256 ? PassShape<C, V>::kCTAs
     const bool full = tile_base + TILE <= a.n;
     const uint32_t valid = full ? TILE : (uint32_t)(a.n - tile_base);
 
+    if (a.prefetch_ahead && t == 0) {
+        // whole tiles only, and only where both ranges are 16-byte aligned
+        const uint64_t pb = ((uint64_t)tile + a.prefetch_ahead) * TILE;
+        if (pb + TILE <= a.n) {
+            const size_t kb = first ? sizeof(In) : sizeof(Cell);
+            const char* kp = static_cast<const char*>(pick_src(a, src, false)) + pb * kb;
+            if (((uintptr_t)kp & 15) == 0) bulk_prefetch_l2(kp, (uint32_t)(TILE * kb));
+            if constexpr (kPairs) {
+                const char* vp = static_cast<const char*>(pick_src(a, src, true)) + pb * sizeof(VS);
+                if (((uintptr_t)vp & 15) == 0) bulk_prefetch_l2(vp, (uint32_t)(TILE * sizeof(VS)));
+            }
+        }
+    }
+
     // ---- load (warp-striped: warp w owns inputs [w*32*IPT, (w+1)*32*IPT)) ----
     const uint64_t wbase = tile_base + (uint64_t)warp * 32 * IPT + lane;
     Cell k[IPT];
     VS v[IPT];
-    const uint32_t src = P->src[a.pass];
     if (first) {
         const In* in = static_cast<const In*>(pick_src(a, src, false)) + wbase;
         bool ok = true;
@@ -523,10 +566,12 @@ __global__ void __launch_bounds__(PB, PB == 256 ? PassShape<C, V>::kCTAs
 
     // ---- stable rank in (cell, input) order, scattered into shared memory ----
     const uint32_t lt = lanemask_lt(), gt = lanemask_gt();
+    constexpr bool kLut = PB == 256 && PassShape<C, V>::kLut && IPT == PassShape<C, V>::kIPT;
+    const LaneBits lb_bits = lane_bits();
 #pragma unroll
     for (int i = 0; i < IPT; i++) {
         const uint32_t d = digit_of(k[i], a.shift);
-        const uint32_t peers = match_digit(d);
+        const uint32_t peers = peer_mask<kLut>(d, lb_bits);
         uint32_t* slot = &ws[warp][d];
         const uint32_t pos0 = *slot;
         const uint32_t below = __popc(peers & lt);
@@ -558,8 +603,8 @@ __global__ void __launch_bounds__(PB, PB == 256 ? PassShape<C, V>::kCTAs
     __syncthreads();
 
     // ---- coalesced write-out: consecutive threads, consecutive positions ----
-    void* kdst = pick_dst(a, P->dst[a.pass], false);
-    VS* vdst = kPairs ? static_cast<VS*>(pick_dst(a, P->dst[a.pass], true)) : nullptr;
+    void* kdst = pick_dst(a, dst, false);
+    VS* vdst = kPairs ? static_cast<VS*>(pick_dst(a, dst, true)) : nullptr;
     // (the clamp of g only acts after a timed-out wait: output unspecified)
     const uint32_t gmax = (uint32_t)a.n - 1u;
     if (last) {

@@ -151,6 +151,7 @@ extern "C" rs_status rs_sort_u32_noalloc(const uint32_t* keys_in, uint32_t* keys
         pa.lookback_next = lb[(p + 1) & 1];
         pa.tile_counter = &plan->tile_counter[p];
         pa.status = status_word;
+        pa.prefetch_ahead = prefetch_ahead_for(PassShape<C, NoVal>::kCTAs * sm_count(device));
         pass_kernel<C, NoVal, IPT, PB><<<(unsigned)L.tiles, PB, Smem::kBytes, st>>>(pa);
     }
     return cudaGetLastError() == cudaSuccess ? RS_OK : RS_ERR_CUDA;

@@ -222,6 +222,7 @@ rs_status run_sort(rs_ctx* ctx, const void* keys_in, void* keys_out, const void*
             return RS_ERR_CUDA;
         smem_set[ctx->device].store(true, std::memory_order_release);
     }
+    const uint32_t ahead = prefetch_ahead_for(PassShape<C, V>::kCTAs * sm_count(ctx->device));
     for (uint32_t p = 0; p < passes; p++) {
         PassArgs a{};
         a.keys_in = keys_in;
@@ -240,6 +241,7 @@ rs_status run_sort(rs_ctx* ctx, const void* keys_in, void* keys_out, const void*
         a.lookback_next = lb[(p + 1) & 1];
         a.tile_counter = &plan->tile_counter[p];
         a.status = ctx->d_status;
+        a.prefetch_ahead = ahead;
         LaunchTimer lt(ctx, KC_PASS, stream);
         kern<<<(unsigned)L.tiles, PB, Smem::kBytes, stream>>>(a);
     }
