@@ -341,6 +341,40 @@ __device__ __forceinline__ uint32_t peer_mask(uint32_t d, const LaneBits& L) {
         return match_digit(d);
 }
 
+// A ranked tile staged in shared memory.  4-byte cells with 4-byte values
+// are kept as one 8-byte item (one shared store per key in the rank, one
+// load per item in the write-out); other shapes keep keys and values in two
+// arrays.
+template <typename Cell, typename VS, bool kPairs, int TILE>
+struct Stage {
+    static constexpr bool kPacked = kPairs && sizeof(Cell) == 4 && sizeof(VS) == 4;
+    unsigned char* base;
+    __device__ __forceinline__ void put(uint32_t pos, Cell k, VS v) const {
+        if constexpr (kPacked) {
+            reinterpret_cast<uint2*>(base)[pos] = make_uint2((uint32_t)k, (uint32_t)v);
+        } else {
+            reinterpret_cast<Cell*>(base)[pos] = k;
+            if constexpr (kPairs) reinterpret_cast<VS*>(base + sizeof(Cell) * TILE)[pos] = v;
+        }
+    }
+    __device__ __forceinline__ Cell key(uint32_t j) const {
+        if constexpr (kPacked)
+            return (Cell)reinterpret_cast<const uint2*>(base)[j].x;
+        else
+            return reinterpret_cast<const Cell*>(base)[j];
+    }
+    __device__ __forceinline__ void get(uint32_t j, Cell& k, VS& v) const {
+        if constexpr (kPacked) {
+            const uint2 kv = reinterpret_cast<const uint2*>(base)[j];
+            k = (Cell)kv.x;
+            v = (VS)kv.y;
+        } else {
+            k = reinterpret_cast<const Cell*>(base)[j];
+            if constexpr (kPairs) v = reinterpret_cast<const VS*>(base + sizeof(Cell) * TILE)[j];
+        }
+    }
+};
+
 template <typename Cell, typename V, int IPT, int PB = BLOCK>
 struct PassSmem {
     static constexpr int TILE = PB * IPT;
@@ -444,8 +478,7 @@ __global__ void __launch_bounds__(PB, PB == 256 ? PassShape<C, V>::kCTAs
     __shared__ uint32_t s_warp[NW];
     __shared__ uint32_t s_tile;
     extern __shared__ __align__(16) unsigned char smem_dyn[];
-    Cell* s_keys = reinterpret_cast<Cell*>(smem_dyn);
-    VS* s_vals = reinterpret_cast<VS*>(smem_dyn + sizeof(Cell) * TILE);
+    const Stage<Cell, VS, kPairs, TILE> stage{smem_dyn};
 
     const uint32_t t = threadIdx.x, lane = lane_id(), warp = t >> 5;
 
@@ -580,8 +613,7 @@ __global__ void __launch_bounds__(PB, PB == 256 ? PassShape<C, V>::kCTAs
         __syncwarp();
         if ((peers & gt) == 0) *slot = pos0 + below + 1;
         const uint32_t pos = pos0 + below;
-        s_keys[pos] = k[i];
-        if constexpr (kPairs) s_vals[pos] = v[i];
+        stage.put(pos, k[i], v[i]);
         __syncwarp();
     }
 
@@ -613,17 +645,21 @@ __global__ void __launch_bounds__(PB, PB == 256 ? PassShape<C, V>::kCTAs
 #pragma unroll
             for (int i = 0; i < IPT; i++) {
                 const uint32_t j = t + i * PB;
-                const Cell c = s_keys[j];
+                Cell c;
+                VS val;
+                stage.get(j, c, val);
                 const uint32_t g = min(s_bin_global[digit_of(c, a.shift)] + j, gmax);
                 __stcs(&out[g], C::encode(c, a.prm));
-                if constexpr (kPairs) __stcs(&vdst[g], s_vals[j]);
+                if constexpr (kPairs) __stcs(&vdst[g], val);
             }
         } else {
             for (uint32_t j = t; j < valid; j += PB) {
-                const Cell c = s_keys[j];
+                Cell c;
+                VS val;
+                stage.get(j, c, val);
                 const uint32_t g = min(s_bin_global[digit_of(c, a.shift)] + j, gmax);
                 __stcs(&out[g], C::encode(c, a.prm));
-                if constexpr (kPairs) __stcs(&vdst[g], s_vals[j]);
+                if constexpr (kPairs) __stcs(&vdst[g], val);
             }
         }
     } else {
@@ -632,17 +668,21 @@ __global__ void __launch_bounds__(PB, PB == 256 ? PassShape<C, V>::kCTAs
 #pragma unroll
             for (int i = 0; i < IPT; i++) {
                 const uint32_t j = t + i * PB;
-                const Cell c = s_keys[j];
+                Cell c;
+                VS val;
+                stage.get(j, c, val);
                 const uint32_t g = min(s_bin_global[digit_of(c, a.shift)] + j, gmax);
                 out[g] = c;
-                if constexpr (kPairs) vdst[g] = s_vals[j];
+                if constexpr (kPairs) vdst[g] = val;
             }
         } else {
             for (uint32_t j = t; j < valid; j += PB) {
-                const Cell c = s_keys[j];
+                Cell c;
+                VS val;
+                stage.get(j, c, val);
                 const uint32_t g = min(s_bin_global[digit_of(c, a.shift)] + j, gmax);
                 out[g] = c;
-                if constexpr (kPairs) vdst[g] = s_vals[j];
+                if constexpr (kPairs) vdst[g] = val;
             }
         }
     }
