@@ -36,7 +36,11 @@ ORACLE_SAMPLE = 1 << 26        # cpu_baseline: oracle on the first 2^26 pairs (~
 REFERENCE_STEP_SAMPLE = 1 << 22
 PASS_BYTES_PER_KEY = 16        # one digit-group pass moves key+value in and out: 4+4+4+4
 COUNT_BYTES_PER_KEY = 4        # the counting pass reads each key once
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "pass_kernel_u32_pairs_2p28.md")
+# DRAM traffic of one pass-kernel launch, measured by ncu and written by
+# `bench.py --ingest-dram-csv` (machine-read; the markdown summaries beside it
+# are for people)
+TRAFFIC_JSON = os.path.join(ROOT, "profiles", "pass_kernel_u32_pairs_traffic.json")
+PASS_KERNEL_NAME = "pass_kernel<CodecU32, unsigned int, 40, 256>"
 
 
 def parse():
@@ -59,6 +63,10 @@ def parse():
                     help="skip the one-call-per-segment comparison (65536 calls)")
     ap.add_argument("--no-run-a", action="store_true",
                     help="skip the 6.2e9-key segmented run (148 GB of device memory)")
+    ap.add_argument("--ingest-dram-csv", metavar="CSV",
+                    help="write the pass kernel's measured DRAM traffic (an ncu --csv capture "
+                         "of dram__bytes_read.sum/dram__bytes_write.sum over runs at --log2n) "
+                         "to profiles/ and exit; nothing runs on the GPU")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the 10x10x10, decimal and string workloads")
     return ap.parse_args()
@@ -163,23 +171,59 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def profile_traffic(kernel_source_hash: str):
-    """Per-launch DRAM bytes of the pass kernel from the committed ncu summary,
-    or None when absent or taken on a different kernel source."""
-    if not os.path.exists(PROFILE_SUMMARY):
+def profile_traffic(kernel_source_hash: str, n: int):
+    """DRAM bytes (read + write) of one pass-kernel launch over n pairs, from
+    the committed ncu capture scaled by the units processed, with the capture
+    itself; None when absent or taken on a different kernel source."""
+    if not os.path.exists(TRAFFIC_JSON):
         return None
-    vals = {}
-    with open(PROFILE_SUMMARY) as f:
-        for line in f:
-            if ":" in line and line.startswith("- "):
-                k, _, v = line[2:].partition(":")
-                vals[k.strip()] = v.strip().strip("`")
-    if vals.get("kernel_source_sha256") != kernel_source_hash:
+    with open(TRAFFIC_JSON) as f:
+        d = json.load(f)
+    if d.get("kernel_source_sha256") != kernel_source_hash:
         return None
-    try:
-        return float(vals["dram_bytes_per_launch"])
-    except (KeyError, ValueError):
-        return None
+    per_launch = d["dram_bytes_read_per_launch"] + d["dram_bytes_write_per_launch"]
+    return {"bytes_per_launch": per_launch * n / d["n_captured"],
+            "captured_n": d["n_captured"], "captured_launches": d["launches"],
+            "read_over_alg": d["dram_bytes_read_per_launch"] / (8 * d["n_captured"]),
+            "write_over_alg": d["dram_bytes_write_per_launch"] / (8 * d["n_captured"])}
+
+
+def ingest_dram_csv(path: str, n: int) -> dict:
+    """Write TRAFFIC_JSON from an ncu --csv capture of the pass kernel's
+    dram__bytes_read.sum / dram__bytes_write.sum over launches of n pairs."""
+    import csv
+    reads, writes, times = {}, {}, {}
+    scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9,
+             "ns": 1e-9, "us": 1e-6, "usecond": 1e-6, "nsecond": 1e-9, "ms": 1e-3, "msecond": 1e-3}
+    with open(path) as f:
+        rows = [r for r in csv.reader(f) if len(r) > 10]
+    hdr = rows[0]
+    ki, mi, ui, vi, ii = (hdr.index(k) for k in ("Kernel Name", "Metric Name", "Metric Unit",
+                                               "Metric Value", "ID"))
+    for r in rows[1:]:
+        if "pass_kernel" not in r[ki]:
+            continue
+        v = float(r[vi].replace(",", "")) * scale.get(r[ui], 1)
+        {"dram__bytes_read.sum": reads, "dram__bytes_write.sum": writes,
+         "gpu__time_duration.sum": times}.get(r[mi], {})[r[ii]] = v
+    ids = sorted(reads, key=int)
+    if not ids:
+        raise SystemExit(f"no pass_kernel dram rows in {path}")
+    rd = sum(reads[i] for i in ids) / len(ids)
+    wr = sum(writes[i] for i in ids) / len(ids)
+    d = {"kernel": PASS_KERNEL_NAME,
+         "kernel_source_sha256": kernel_source_hash(),
+         "n_captured": n, "launches": len(ids),
+         "dram_bytes_read_per_launch": rd, "dram_bytes_write_per_launch": wr,
+         "alg_bytes_per_launch": PASS_BYTES_PER_KEY * n,
+         "traffic_over_alg": (rd + wr) / (PASS_BYTES_PER_KEY * n),
+         "ncu_ms_per_launch": (sum(times.values()) / len(times) * 1e3) if times else None,
+         "note": "one launch per digit group of one sort; cold caches, serialised; the write "
+                 "figure leaves out lines still dirty in L2 when the launch ends"}
+    with open(TRAFFIC_JSON, "w") as f:
+        json.dump(d, f, indent=1)
+        f.write("\n")
+    return d
 
 
 def kernel_source_hash() -> str:
@@ -944,7 +988,8 @@ def run_ours(args):
     head = results[dists[0]]
     pass_ms = head["pass_ms_avg"]
     achieved = PASS_BYTES_PER_KEY * n / (pass_ms * 1e-3) / 1e9
-    traffic = profile_traffic(kernel_source_hash())
+    traffic_rec = profile_traffic(kernel_source_hash(), n)
+    traffic = traffic_rec["bytes_per_launch"] if traffic_rec else None
     line = {
         "metric": METRIC,
         "value": head["keys_per_s"],
@@ -963,6 +1008,8 @@ def run_ours(args):
                        / (head["ms_per_step"] * 1e-3) / 1e9,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": traffic,
+                     "traffic_over_alg": (traffic / (PASS_BYTES_PER_KEY * n)) if traffic else None,
+                     "traffic_source": traffic_rec,
                      "kernel": f"pass_kernel<CodecU32,u32,{head['ipt']},256>",
                      "alg_bytes_per_launch": PASS_BYTES_PER_KEY * n,
                      "launch_ms_avg": pass_ms, "peak_kind": f"{peak_kind} hbm_gbs"},
@@ -986,6 +1033,9 @@ def run_ours(args):
 
 def main():
     args = parse()
+    if args.ingest_dram_csv:
+        print(json.dumps(ingest_dram_csv(args.ingest_dram_csv, 1 << args.log2n), indent=1))
+        return 0
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -358,8 +358,7 @@ __global__ void __launch_bounds__(BLOCK, seg_ctas_per_sm<C, V>()) seg_sort_kerne
     __shared__ uint32_t s_first, s_take;
     __shared__ uint32_t s_active[MAX_PASSES];
     extern __shared__ __align__(16) unsigned char smem_dyn[];
-    Cell* s_keys = reinterpret_cast<Cell*>(smem_dyn);
-    VS* s_vals = reinterpret_cast<VS*>(smem_dyn + sizeof(Cell) * SEG_TILE);
+    const Stage<Cell, VS, kPairs, SEG_TILE> stage{smem_dyn};
     const uint32_t t = threadIdx.x, lane = lane_id(), warp = t >> 5;
 
     while (true) {
@@ -401,18 +400,14 @@ __global__ void __launch_bounds__(BLOCK, seg_ctas_per_sm<C, V>()) seg_sort_kerne
             load_tile<C, VS, kPairs, true>(a.keys_in, vin, lo, valid, a.prm,
                                            a.iota ? lo : ~0ull, k, v, a.status);
             for (uint32_t p = 0; p < a.passes; p++) {
-                rank_scatter<Cell, VS, SEG_IPT, kPairs>(k, v, valid, p * RADIX_BITS, ts,
-                                                        s_keys, s_vals);
+                rank_scatter<Cell, VS, SEG_IPT, kPairs>(k, v, valid, p * RADIX_BITS, ts, stage);
                 const uint32_t w0 = warp * 32 * SEG_IPT + lane;
 #pragma unroll
                 for (int i = 0; i < SEG_IPT; i++) {
                     const uint32_t j = w0 + i * 32;
-                    if (j < valid) {
-                        k[i] = s_keys[j];
-                        if constexpr (kPairs) v[i] = s_vals[j];
-                    }
+                    if (j < valid) stage.get(j, k[i], v[i]);
                 }
-                __syncthreads();  // s_keys is rewritten by the next group
+                __syncthreads();  // the staged tile is rewritten by the next group
             }
             const uint32_t w0 = warp * 32 * SEG_IPT + lane;
 #pragma unroll
@@ -523,22 +518,23 @@ __global__ void __launch_bounds__(BLOCK, seg_ctas_per_sm<C, V>()) seg_sort_kerne
                 else
                     load_tile<C, VS, kPairs, false>(ksrc, vsrc, base, valid, a.prm, ~0ull, k, v,
                                                     a.status);
-                rank_scatter<Cell, VS, SEG_IPT, kPairs>(k, v, valid, shift, ts, s_keys, s_vals,
-                                                        s_run);
+                rank_scatter<Cell, VS, SEG_IPT, kPairs>(k, v, valid, shift, ts, stage, s_run);
                 for (uint32_t j = t; j < valid; j += BLOCK) {
-                    const Cell c = s_keys[j];
+                    Cell c;
+                    VS val;
+                    stage.get(j, c, val);
                     const uint32_t d = digit_of(c, shift);
                     const uint64_t g = s_run[d] + (j - ts.excl[d]);  // within the segment
                     if (last)
                         static_cast<Out*>(kdst)[g] = C::encode(c, a.prm);
                     else
                         static_cast<Cell*>(kdst)[g] = c;
-                    if constexpr (kPairs) vdst[g] = s_vals[j];
+                    if constexpr (kPairs) vdst[g] = val;
                 }
                 // (the next tile's rank_scatter moves s_run on after its
                 // first barrier, once every thread is past this write-out)
             }
-            // the write-out above reads s_run, s_keys and ts: done before the
+            // the write-out above reads s_run, the staged tile and ts: done before the
             // next group resets them; also orders this group's global writes
             // before the next group's reads
             __syncthreads();
@@ -573,8 +569,9 @@ __global__ void __launch_bounds__(BLOCK, 2) seg_pass_kernel(SegArgs a, uint32_t 
     __shared__ uint32_t s_warp[WARPS];
     __shared__ uint32_t s_tile;
     extern __shared__ __align__(16) unsigned char smem_dyn[];
-    Cell* s_keys = reinterpret_cast<Cell*>(smem_dyn);
-    VS* s_vals = reinterpret_cast<VS*>(smem_dyn + sizeof(Cell) * TILE);
+    const Stage<Cell, VS, kPairs, TILE> stage{smem_dyn};
+    constexpr bool kLut = PassShape<C, V>::kLut && IPT == PassShape<C, V>::kIPT;
+    const LaneBits lbits = lane_bits();
 
     const uint32_t t = threadIdx.x, lane = lane_id(), warp = t >> 5;
     const uint32_t lt_mask = lanemask_lt(), gt_mask = lanemask_gt();
@@ -692,15 +689,14 @@ __global__ void __launch_bounds__(BLOCK, 2) seg_pass_kernel(SegArgs a, uint32_t 
 #pragma unroll
         for (int i = 0; i < IPT; i++) {
             const uint32_t dk = digit_of(k[i], shift);
-            const uint32_t peers = match_digit(dk);
+            const uint32_t peers = peer_mask<kLut>(dk, lbits);
             uint32_t* slot_p = &ws[warp][dk];
             const uint32_t pos0 = *slot_p;
             const uint32_t below = __popc(peers & lt_mask);
             __syncwarp();
             if ((peers & gt_mask) == 0) *slot_p = pos0 + below + 1;
             const uint32_t pos = pos0 + below;
-            s_keys[pos] = k[i];
-            if constexpr (kPairs) s_vals[pos] = v[i];
+            stage.put(pos, k[i], v[i]);
             __syncwarp();
         }
 
@@ -723,23 +719,27 @@ __global__ void __launch_bounds__(BLOCK, 2) seg_pass_kernel(SegArgs a, uint32_t 
             Out* out = static_cast<Out*>(a.keys_out) + lo;
             VS* vout = kPairs ? static_cast<VS*>(a.vals_out) + lo : nullptr;
             for (uint32_t j = t; j < valid; j += BLOCK) {
-                const Cell c = s_keys[j];
+                Cell c;
+                VS val;
+                stage.get(j, c, val);
                 const uint32_t gp = min(s_bin[digit_of(c, shift)] + j, gmax);
                 __stcs(&out[gp], C::encode(c, a.prm));
-                if constexpr (kPairs) __stcs(&vout[gp], s_vals[j]);
+                if constexpr (kPairs) __stcs(&vout[gp], val);
             }
         } else {
             Cell* out = dstb == BUF_TMP ? tmp_cells : out_cells;
             VS* vout = kPairs ? static_cast<VS*>(dstb == BUF_TMP ? a.vals_tmp : a.vals_out) + lo
                               : nullptr;
             for (uint32_t j = t; j < valid; j += BLOCK) {
-                const Cell c = s_keys[j];
+                Cell c;
+                VS val;
+                stage.get(j, c, val);
                 const uint32_t gp = min(s_bin[digit_of(c, shift)] + j, gmax);
                 out[gp] = c;
-                if constexpr (kPairs) vout[gp] = s_vals[j];
+                if constexpr (kPairs) vout[gp] = val;
             }
         }
-        __syncthreads();  // s_keys, s_bin and s_tile are reused by the next tile
+        __syncthreads();  // the staged tile, s_bin and s_tile are reused by the next tile
     }
 }
 

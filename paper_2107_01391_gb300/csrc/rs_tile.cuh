@@ -21,16 +21,18 @@ struct TileShared {
 };
 
 // Positions [0, n_valid) of the tile hold keys; the rest are ignored.
-// Returns with s_keys/s_vals holding the tile in (cell, input) order and
+// Returns with `stage` holding the tile in (cell, input) order and
 // ts.count / ts.excl filled.  Every thread of the CTA must call it.
 // s_run (optional): running per-cell output offsets of a sweep over several
 // tiles; the previous tile's ts.count is added to them once every thread is
 // past its write-out (the first barrier below), so the sweep itself needs
 // no barrier between tiles.
-template <typename Cell, typename VS, int IPT, bool kPairs>
+// kLut: the table match (match_digit_lut) in place of match_digit, for
+// shapes whose register budget holds its five lane constants.
+template <typename Cell, typename VS, int IPT, bool kPairs, bool kLut = false, int STILE>
 __device__ __forceinline__ void rank_scatter(const Cell (&k)[IPT], const VS (&v)[IPT],
                                              uint32_t n_valid, uint32_t shift, TileShared& ts,
-                                             Cell* s_keys, VS* s_vals,
+                                             const Stage<Cell, VS, kPairs, STILE>& stage,
                                              uint32_t* s_run = nullptr) {
     const uint32_t t = threadIdx.x, lane = lane_id(), warp = t >> 5;
     const uint32_t wbase = warp * 32 * IPT;
@@ -59,22 +61,21 @@ __device__ __forceinline__ void rank_scatter(const Cell (&k)[IPT], const VS (&v)
     __syncthreads();
 
     const uint32_t lt = lanemask_lt(), gt = lanemask_gt();
+    const LaneBits lbits = lane_bits();
 #pragma unroll
     for (int i = 0; i < IPT; i++) {
         if ((uint32_t)i * 32 >= warp_items) break;  // warp-uniform
         const bool valid = (uint32_t)i * 32 + lane < warp_items;
         const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
         const uint32_t d = digit_of(k[i], shift);
-        const uint32_t peers = match_digit(d) & vmask;
+        const uint32_t peers = peer_mask<kLut>(d, lbits) & vmask;
         uint32_t* slot = &ts.wh[warp][d];
         const uint32_t at = valid ? *slot : 0u;
         const uint32_t below = __popc(peers & lt);
         __syncwarp();
         if (valid) {
             if ((peers & gt) == 0) *slot = at + below + 1;
-            const uint32_t pos = at + below;
-            s_keys[pos] = k[i];
-            if constexpr (kPairs) s_vals[pos] = v[i];
+            stage.put(at + below, k[i], v[i]);
         }
         __syncwarp();
     }
@@ -129,8 +130,9 @@ __global__ void __launch_bounds__(BLOCK, 2) tile_rows_kernel(RowsArgs a) {
     __shared__ TileShared ts;
     __shared__ Cell s_ref;
     extern __shared__ __align__(16) unsigned char smem_dyn[];
-    Cell* s_keys = reinterpret_cast<Cell*>(smem_dyn);
-    VS* s_vals = reinterpret_cast<VS*>(smem_dyn + sizeof(Cell) * TILE);
+    const Stage<Cell, VS, kPairs, TILE> stage{smem_dyn};
+    // the table match where the 32-key rows leave room for its constants
+    constexpr bool kLut = IPT == ROW_IPT && sizeof(Cell) == 4 && sizeof(VS) == 4;
     const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
     const uint32_t w0 = warp * 32 * IPT + lane;  // warp-striped: input order
     const uint32_t n = a.len;
@@ -165,16 +167,13 @@ __global__ void __launch_bounds__(BLOCK, 2) tile_rows_kernel(RowsArgs a) {
                 if (w0 + i * 32 < n) same &= digit_of(k[i], shift) == digit_of(ref, shift);
             if (__syncthreads_and(same)) continue;  // every key in one cell
             moved++;
-            rank_scatter<Cell, VS, IPT, kPairs>(k, v, n, shift, ts, s_keys, s_vals);
+            rank_scatter<Cell, VS, IPT, kPairs, kLut>(k, v, n, shift, ts, stage);
 #pragma unroll
             for (int i = 0; i < IPT; i++) {
                 const uint32_t j = w0 + i * 32;
-                if (j < n) {
-                    k[i] = s_keys[j];
-                    if constexpr (kPairs) v[i] = s_vals[j];
-                }
+                if (j < n) stage.get(j, k[i], v[i]);
             }
-            __syncthreads();  // s_keys is rewritten by the next group
+            __syncthreads();  // the staged tile is rewritten by the next group
         }
 #pragma unroll
         for (int i = 0; i < IPT; i++) {
