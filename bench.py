@@ -229,7 +229,7 @@ def ingest_dram_csv(path: str, n: int) -> dict:
 def kernel_source_hash() -> str:
     import hashlib
     h = hashlib.sha256()
-    for name in ("rs_device.cuh", "rs_kernels.cuh"):
+    for name in ("rs_device.cuh", "rs_kernels.cuh", "rs_sort_impl.cuh"):
         with open(os.path.join(ROOT, "paper_2107_01391_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
