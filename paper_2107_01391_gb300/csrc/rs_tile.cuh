@@ -28,8 +28,11 @@ struct TileShared {
 // past its write-out (the first barrier below), so the sweep itself needs
 // no barrier between tiles.
 // kLut: the table match (match_digit_lut) in place of match_digit, for
-// shapes whose register budget holds its five lane constants.
-template <typename Cell, typename VS, int IPT, bool kPairs, bool kLut = false, int STILE>
+// shapes whose register budget holds its five lane constants.  kFull: every
+// position of the tile holds a key (n_valid == BLOCK * IPT), so no position
+// is tested.
+template <typename Cell, typename VS, int IPT, bool kPairs, bool kLut = false,
+          bool kFull = false, int STILE>
 __device__ __forceinline__ void rank_scatter(const Cell (&k)[IPT], const VS (&v)[IPT],
                                              uint32_t n_valid, uint32_t shift, TileShared& ts,
                                              const Stage<Cell, VS, kPairs, STILE>& stage,
@@ -38,10 +41,12 @@ __device__ __forceinline__ void rank_scatter(const Cell (&k)[IPT], const VS (&v)
     const uint32_t wbase = warp * 32 * IPT;
     for (uint32_t d = lane; d < RADIX; d += 32) ts.wh[warp][d] = 0;
     __syncwarp();
-    const uint32_t warp_items = wbase < n_valid ? min(n_valid - wbase, 32u * IPT) : 0u;
+    const uint32_t warp_items =
+        kFull ? 32u * IPT : (wbase < n_valid ? min(n_valid - wbase, 32u * IPT) : 0u);
 #pragma unroll
     for (int i = 0; i < IPT; i++)
-        if ((uint32_t)i * 32 + lane < warp_items) atomicAdd(&ts.wh[warp][digit_of(k[i], shift)], 1u);
+        if (kFull || (uint32_t)i * 32 + lane < warp_items)
+            atomicAdd(&ts.wh[warp][digit_of(k[i], shift)], 1u);
     __syncthreads();
 
     uint32_t run = 0;
@@ -64,9 +69,9 @@ __device__ __forceinline__ void rank_scatter(const Cell (&k)[IPT], const VS (&v)
     const LaneBits lbits = lane_bits();
 #pragma unroll
     for (int i = 0; i < IPT; i++) {
-        if ((uint32_t)i * 32 >= warp_items) break;  // warp-uniform
-        const bool valid = (uint32_t)i * 32 + lane < warp_items;
-        const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
+        if (!kFull && (uint32_t)i * 32 >= warp_items) break;  // warp-uniform
+        const bool valid = kFull || (uint32_t)i * 32 + lane < warp_items;
+        const uint32_t vmask = kFull ? 0xffffffffu : __ballot_sync(0xffffffffu, valid);
         const uint32_t d = digit_of(k[i], shift);
         const uint32_t peers = peer_mask<kLut>(d, lbits) & vmask;
         uint32_t* slot = &ts.wh[warp][d];
@@ -113,14 +118,84 @@ struct RowsArgs {
     const uint32_t* skip;  // nullable; non-zero at run time: the sort is a no-op
 };
 
+// One row: load, one rank per non-trivial digit group, write.  kFull: the
+// row fills the tile (n == BLOCK * IPT), so no position is tested.
+template <class C, typename V, int IPT, typename VR, bool kFull>
+__device__ __forceinline__ uint32_t sort_row(const RowsArgs& a, uint64_t row, TileShared& ts,
+                                             typename C::Cell& s_ref,
+                                             const Stage<typename C::Cell,
+                                                         typename std::conditional<
+                                                             ValTraits<V>::kPairs, VR,
+                                                             uint32_t>::type,
+                                                         ValTraits<V>::kPairs,
+                                                         BLOCK * IPT>& stage) {
+    using Cell = typename C::Cell;
+    using In = typename C::In;
+    using Out = typename C::Out;
+    constexpr bool kPairs = ValTraits<V>::kPairs;
+    using VS = typename std::conditional<kPairs, VR, uint32_t>::type;
+    using VM = typename std::conditional<kPairs, V, uint32_t>::type;
+    // the table match where the 32-key rows leave room for its constants
+    constexpr bool kLut = IPT == ROW_IPT && sizeof(Cell) == 4 && sizeof(VS) == 4;
+    const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+    const uint32_t w0 = warp * 32 * IPT + lane;  // warp-striped: input order
+    const uint32_t n = a.len;
+    const uint64_t base = row * n;
+    Cell k[IPT];
+    VS v[IPT];
+    bool ok = true;
+#pragma unroll
+    for (int i = 0; i < IPT; i++) {
+        const uint32_t j = w0 + i * 32;
+        k[i] = ~Cell(0);
+        v[i] = VS(0);
+        if (kFull || j < n) {
+            k[i] = C::decode(static_cast<const In*>(a.keys_in)[base + j], a.prm, ok);
+            if constexpr (kPairs)
+                v[i] = a.iota ? (VS)j : (VS) static_cast<const VM*>(a.vals_in)[base + j];
+        }
+    }
+    if (!ok) atomicOr(a.status, STATUS_RANGE);
+    if (threadIdx.x == 0) s_ref = k[0];  // the row's first key
+    __syncthreads();
+    const Cell ref = s_ref;
+    uint32_t moved = 0;
+    for (uint32_t p = 0; p < a.passes; p++) {
+        const uint32_t shift = p * RADIX_BITS;
+        bool same = true;
+#pragma unroll
+        for (int i = 0; i < IPT; i++)
+            if (kFull || w0 + i * 32 < n) same &= digit_of(k[i], shift) == digit_of(ref, shift);
+        if (__syncthreads_and(same)) continue;  // every key in one cell
+        moved++;
+        rank_scatter<Cell, VS, IPT, kPairs, kLut, kFull>(k, v, n, shift, ts, stage);
+#pragma unroll
+        for (int i = 0; i < IPT; i++) {
+            const uint32_t j = w0 + i * 32;
+            if (kFull || j < n) stage.get(j, k[i], v[i]);
+        }
+        __syncthreads();  // the staged tile is rewritten by the next group
+    }
+#pragma unroll
+    for (int i = 0; i < IPT; i++) {
+        const uint32_t j = w0 + i * 32;
+        if (kFull || j < n) {
+            static_cast<Out*>(a.keys_out)[base + j] = C::encode(k[i], a.prm);
+            if constexpr (kPairs) static_cast<VM*>(a.vals_out)[base + j] = (VM)v[i];
+        }
+    }
+    return moved;
+}
+
 // VR: the type a value is carried in through the passes (registers and
 // shared memory); V is its type in memory.  An argsort's indices are below
 // BLOCK * IPT, so they travel as 32-bit words whatever their output width.
+// At the start of each row the CTA prefetches its next row (row + gridDim.x)
+// into L2 with one TMA bulk prefetch, so that row's loads do not wait on DRAM.
 template <class C, typename V, int IPT, typename VR = V>
 __global__ void __launch_bounds__(BLOCK, 2) tile_rows_kernel(RowsArgs a) {
     using Cell = typename C::Cell;
     using In = typename C::In;
-    using Out = typename C::Out;
     constexpr bool kPairs = ValTraits<V>::kPairs;
     constexpr uint32_t TILE = BLOCK * IPT;
     using VS = typename std::conditional<kPairs, VR, uint32_t>::type;
@@ -131,58 +206,25 @@ __global__ void __launch_bounds__(BLOCK, 2) tile_rows_kernel(RowsArgs a) {
     __shared__ Cell s_ref;
     extern __shared__ __align__(16) unsigned char smem_dyn[];
     const Stage<Cell, VS, kPairs, TILE> stage{smem_dyn};
-    // the table match where the 32-key rows leave room for its constants
-    constexpr bool kLut = IPT == ROW_IPT && sizeof(Cell) == 4 && sizeof(VS) == 4;
-    const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
-    const uint32_t w0 = warp * 32 * IPT + lane;  // warp-striped: input order
     const uint32_t n = a.len;
     uint32_t moved = 0;
 
     for (uint64_t row = blockIdx.x; row < a.rows; row += gridDim.x) {
-        const uint64_t base = row * n;
-        Cell k[IPT];
-        VS v[IPT];
-        bool ok = true;
-#pragma unroll
-        for (int i = 0; i < IPT; i++) {
-            const uint32_t j = w0 + i * 32;
-            k[i] = ~Cell(0);
-            v[i] = VS(0);
-            if (j < n) {
-                k[i] = C::decode(static_cast<const In*>(a.keys_in)[base + j], a.prm, ok);
-                if constexpr (kPairs)
-                    v[i] = a.iota ? (VS)j : (VS) static_cast<const VM*>(a.vals_in)[base + j];
+        const uint64_t next = row + gridDim.x;
+        if (threadIdx.x == 0 && next < a.rows) {
+            const char* kp = static_cast<const char*>(a.keys_in) + next * n * sizeof(In);
+            const uint32_t kb = n * (uint32_t)sizeof(In);
+            if ((((uintptr_t)kp | kb) & 15) == 0) bulk_prefetch_l2(kp, kb);
+            if (kPairs && !a.iota) {
+                const char* vp = static_cast<const char*>(a.vals_in) + next * n * sizeof(VM);
+                const uint32_t vb = n * (uint32_t)sizeof(VM);
+                if ((((uintptr_t)vp | vb) & 15) == 0) bulk_prefetch_l2(vp, vb);
             }
         }
-        if (!ok) atomicOr(a.status, STATUS_RANGE);
-        if (threadIdx.x == 0) s_ref = k[0];  // the row's first key
-        __syncthreads();
-        const Cell ref = s_ref;
-        moved = 0;
-        for (uint32_t p = 0; p < a.passes; p++) {
-            const uint32_t shift = p * RADIX_BITS;
-            bool same = true;
-#pragma unroll
-            for (int i = 0; i < IPT; i++)
-                if (w0 + i * 32 < n) same &= digit_of(k[i], shift) == digit_of(ref, shift);
-            if (__syncthreads_and(same)) continue;  // every key in one cell
-            moved++;
-            rank_scatter<Cell, VS, IPT, kPairs, kLut>(k, v, n, shift, ts, stage);
-#pragma unroll
-            for (int i = 0; i < IPT; i++) {
-                const uint32_t j = w0 + i * 32;
-                if (j < n) stage.get(j, k[i], v[i]);
-            }
-            __syncthreads();  // the staged tile is rewritten by the next group
-        }
-#pragma unroll
-        for (int i = 0; i < IPT; i++) {
-            const uint32_t j = w0 + i * 32;
-            if (j < n) {
-                static_cast<Out*>(a.keys_out)[base + j] = C::encode(k[i], a.prm);
-                if constexpr (kPairs) static_cast<VM*>(a.vals_out)[base + j] = (VM)v[i];
-            }
-        }
+        if (n == TILE)
+            moved = sort_row<C, V, IPT, VR, true>(a, row, ts, s_ref, stage);
+        else
+            moved = sort_row<C, V, IPT, VR, false>(a, row, ts, s_ref, stage);
     }
     if (a.info && blockIdx.x == 0 && threadIdx.x == 0) {
         a.info->mode = MODE_PASSES;
