@@ -166,11 +166,14 @@ rs_status rs_sort_pairs(rs_ctx* ctx, rs_key_type kt, const void* keys_in, void* 
  *             smallest string (equal strings keep input order).
  * A string longer than max_len, or offsets that decrease or pass offsets[n],
  * raise RS_ERR_RANGE (device-detected); such strings are cut to fit and the
- * output is unspecified.  Cost: positions are sorted in chunks of
- * floor(64 / w) symbols (w = bits per symbol of the alphabet present, 5 for
- * 'a'..'z'); a chunk wholly past the longest string is skipped on the device,
- * but its launches still run (about 65 us per skipped chunk at 2^24
- * strings), so a max_len close to the longest string is cheapest. */
+ * output is unspecified.  Cost: the strings are first sorted by their
+ * leading floor(56 / w) symbols (w = bits per symbol of the alphabet present,
+ * 5 for 'a'..'z', so 11 symbols in seven digit passes).  Only when two strings
+ * agree on those symbols and either is longer does a second, general sort
+ * run: positions in chunks of floor(64 / w) symbols, least significant chunk
+ * first.  Its launches always run but exit at once on the device when it is
+ * not needed (a chunk wholly past the longest string is skipped too), so a
+ * max_len close to the longest string is cheapest. */
 #define RS_MAX_STRING_LEN 1024u
 rs_status rs_sort_strings(rs_ctx* ctx, const uint8_t* chars, const uint32_t* offsets, size_t n,
                           uint32_t max_len, uint32_t* perm_out, void* temp, size_t* temp_bytes,

@@ -488,18 +488,24 @@ __global__ void __launch_bounds__(PB, PB == 256 ? PassShape<C, V>::kCTAs
     uint32_t claimed = 0;
     if (t == 0) claimed = atomicAdd(a.tile_counter, 1u);
 
-    // The next pass's look-back rows are free once this pass started: clear
-    // one row per CTA (the grid has one CTA per tile).
-#pragma unroll
-    for (int e = 0; e < ND; e++) a.lookback_next[(uint64_t)blockIdx.x * RADIX + e * PB + t] = 0;
-    for (uint32_t d = lane; d < RADIX; d += 32) ws[warp][d] = 0;
-
     // every plan word this pass reads, loaded together: one round trip that
     // overlaps the tile claim (the plan was written by an earlier launch)
     const DevPlan* P = a.plan;
     const uint32_t p_mode = __ldg(&P->mode), p_active = __ldg(&P->active[a.pass]);
     const uint32_t p_first = __ldg(&P->first_active), p_last = __ldg(&P->last_active);
     const uint32_t src = __ldg(&P->src[a.pass]), dst = __ldg(&P->dst[a.pass]);
+
+    // The next pass's look-back rows are free once this pass started: clear
+    // one row per CTA (the grid has one CTA per tile), unless no later pass
+    // moves data (the last active pass, the rebuild from cells, or a sort
+    // skipped as a whole, whose plan stays zeroed), so that a sort the
+    // device skips costs little more than its launches.
+    if (p_mode == MODE_PASSES && p_last != MAX_PASSES && p_last > a.pass) {
+#pragma unroll
+        for (int e = 0; e < ND; e++)
+            a.lookback_next[(uint64_t)blockIdx.x * RADIX + e * PB + t] = 0;
+    }
+    for (uint32_t d = lane; d < RADIX; d += 32) ws[warp][d] = 0;
     if (p_mode != MODE_PASSES || !p_active) return;
     const bool first = p_first == a.pass;
     const bool last = p_last == a.pass;

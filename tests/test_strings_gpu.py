@@ -109,6 +109,31 @@ def test_edge_strings(rs, ctx, oracle, case):
     assert np.array_equal(got, ref.astype(np.uint32))
 
 
+@pytest.mark.parametrize("case", ["differ_after_11", "equal_11", "mixed_lengths"])
+def test_first_attempt_boundary(rs, ctx, oracle, case):
+    """The first attempt sorts by the leading 11 symbols of a 'a'..'z'
+    alphabet (56 bits of 5-bit symbols).  Strings that agree there and are
+    longer must go through the general sort; strings of at most 11 symbols
+    that agree there are equal and keep their input order."""
+    rng = np.random.default_rng(len(case))
+    head = [bytes(rng.integers(97, 123, 11).astype(np.uint8)) for _ in range(50)]
+    strs = []
+    for _ in range(20_000):
+        h = head[int(rng.integers(0, len(head)))]
+        if case == "differ_after_11":
+            strs.append(h + bytes(rng.integers(97, 123, int(rng.integers(1, 6))).astype(np.uint8)))
+        elif case == "equal_11":
+            strs.append(h)
+        else:
+            tail = int(rng.integers(0, 3))
+            strs.append(h[: int(rng.integers(9, 12))] if tail == 0 else
+                        h + bytes(rng.integers(97, 123, tail).astype(np.uint8)))
+    chars, offsets = _pack(strs)
+    ref, _ = oracle.sort_strings(chars, offsets.astype(np.uint64))
+    got = _gpu_perm(rs, ctx, chars, offsets, 16)
+    assert np.array_equal(got, ref.astype(np.uint32))
+
+
 def test_all_empty_strings(rs, ctx):
     n = 777
     chars = np.zeros(0, np.uint8)
