@@ -518,7 +518,11 @@ __global__ void __launch_bounds__(BLOCK, seg_ctas_per_sm<C, V>()) seg_sort_kerne
                 else
                     load_tile<C, VS, kPairs, false>(ksrc, vsrc, base, valid, a.prm, ~0ull, k, v,
                                                     a.status);
-                rank_scatter<Cell, VS, SEG_IPT, kPairs>(k, v, valid, shift, ts, stage, s_run);
+                if (valid == SEG_TILE)  // every tile but a segment's last: no position tests
+                    rank_scatter<Cell, VS, SEG_IPT, kPairs, false, true>(k, v, valid, shift, ts,
+                                                                         stage, s_run);
+                else
+                    rank_scatter<Cell, VS, SEG_IPT, kPairs>(k, v, valid, shift, ts, stage, s_run);
                 for (uint32_t j = t; j < valid; j += BLOCK) {
                     Cell c;
                     VS val;
