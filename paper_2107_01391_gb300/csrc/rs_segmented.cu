@@ -73,6 +73,17 @@ struct SegControl {
     uint32_t long_tiles;               // device tiles of segments counted tile-parallel
 };
 
+// One device tile, written when tiles are handed out (seg_tiles_kernel) and
+// completed with the segment's moving digit groups when the segment is
+// counted (seg_sort_kernel): everything a device-tier pass needs to start
+// loading the tile, in one 16-byte read after its claim.
+struct TileMeta {
+    uint64_t lo;      // first key of the owning segment
+    uint32_t len;     // keys in the segment (at most RS_MAX_N)
+    uint32_t lt_use;  // bits 0..23: tile index within the segment; 24..31: moving groups
+};
+static_assert(sizeof(TileMeta) == 16, "one 16-byte load");
+
 struct SegArgs {
     const void* keys_in;
     void* keys_out;
@@ -97,6 +108,7 @@ struct SegArgs {
     uint32_t* tile_start;  // [n_large] first device tile of the segment
     uint32_t* tile_owner;  // [max_tiles] order index of the segment owning a tile
     uint32_t* long_tile;   // [max_tiles] the device tiles of segments of count_par_min keys or more
+    TileMeta* tile_meta;   // [max_tiles]
     uint32_t* lookback[2];
     uint64_t max_tiles;
     uint32_t n_large_max;  // room of bins, dev_use and tile_start
@@ -182,7 +194,14 @@ __global__ void __launch_bounds__(BLOCK) seg_tiles_kernel(SegArgs a) {
             continue;
         }
         a.tile_start[i] = start;
-        for (uint32_t j = 0; j < tiles; j++) a.tile_owner[start + j] = (uint32_t)i;
+        for (uint32_t j = 0; j < tiles; j++) {
+            a.tile_owner[start + j] = (uint32_t)i;
+            TileMeta m;
+            m.lo = lo;
+            m.len = (uint32_t)(hi - lo);
+            m.lt_use = j;  // the moving groups are added when the segment is counted
+            a.tile_meta[start + j] = m;
+        }
         // a long segment's tiles are listed for seg_count_kernel, which adds
         // their counts into the segment's rows of bins: they start at zero
         if (hi - lo >= a.count_par_min) {
@@ -475,6 +494,12 @@ __global__ void __launch_bounds__(BLOCK, seg_ctas_per_sm<C, V>()) seg_sort_kerne
         if (device_tier) {
             // the device tier moves this segment: its starts are stored above
             if (t == 0) a.dev_use[first_w] = use;
+            const uint32_t ts0 = a.tile_start[first_w];
+            if (ts0 != 0xffffffffu) {
+                const uint32_t ntiles = (uint32_t)((len + a.dev_tile - 1) / a.dev_tile);
+                for (uint32_t j = t; j < ntiles; j += BLOCK)
+                    a.tile_meta[ts0 + j].lt_use = j | (use << 24);
+            }
             continue;  // (s_hist is cleared again after the next loop-top barrier)
         }
 
@@ -592,24 +617,20 @@ __global__ void __launch_bounds__(BLOCK, 2) seg_pass_kernel(SegArgs a, uint32_t 
         const uint32_t g = s_tile;
         if (g >= dev_tiles) return;
         lookback_next[(uint64_t)g * RADIX + t] = 0;  // the next group's row of this tile
-        // the owner; every thread reads the same words, so the tests are uniform
-        const uint32_t slot = a.tile_owner[g];
-        uint64_t lo = 0, hi = 0;
-        uint32_t first_tile = 0, use = 0;
-        bool ok = slot < n_large;
-        if (ok) {
-            first_tile = a.tile_start[slot];
-            use = a.dev_use[slot];
-            ok = seg_bounds(a, a.order[slot], lo, hi) && first_tile != 0xffffffffu &&
-                 g >= first_tile && (uint64_t)(g - first_tile) * TILE < hi - lo;
-        }
+        // the tile's description and owner, one round trip; every thread reads
+        // the same words, so the tests are uniform
+        const uint4 mw = __ldcg(reinterpret_cast<const uint4*>(&a.tile_meta[g]));
+        const uint32_t slot = __ldcg(&a.tile_owner[g]);
+        const uint64_t lo = (uint64_t)mw.x | ((uint64_t)mw.y << 32);
+        const uint64_t len = mw.z;
+        const uint32_t lt = mw.w & 0xffffffu;  // tile index within the segment
+        const uint32_t use = mw.w >> 24;
+        const uint64_t tbase = (uint64_t)lt * TILE;
+        const bool ok = slot < n_large && tbase < len && lo + len <= a.n;
         if (!ok || !(use >> pass & 1u)) {
             __syncthreads();  // everyone has read s_tile before the next claim
             continue;
         }
-        const uint32_t lt = g - first_tile;  // tile index within the segment
-        const uint64_t len = hi - lo;
-        const uint64_t tbase = (uint64_t)lt * TILE;
         const bool full = tbase + TILE <= len;
         const uint32_t valid = full ? TILE : (uint32_t)(len - tbase);
         const uint32_t from_end = __popc(use) - 1 - __popc(use & ((1u << pass) - 1u));
@@ -754,7 +775,7 @@ __global__ void __launch_bounds__(BLOCK, 2) seg_pass_kernel(SegArgs a, uint32_t 
 // entry of the list of tiles counted tile-parallel, and two look-back rows.
 struct SegLayout {
     size_t ctl, order, keys_tmp, vals_tmp, bins, dev_use, tile_start, tile_owner, long_tile,
-        lookback0, lookback1, total;
+        tile_meta, lookback0, lookback1, total;
     size_t n_large_max, max_tiles;
 };
 
@@ -777,6 +798,7 @@ inline SegLayout seg_layout(size_t n, size_t num_segs, bool equal_segments, size
     L.tile_start = at;  at += align_up(sizeof(uint32_t) * L.n_large_max);
     L.tile_owner = at;  at += align_up(sizeof(uint32_t) * L.max_tiles);
     L.long_tile = at;   at += align_up(sizeof(uint32_t) * L.max_tiles);
+    L.tile_meta = at;   at += align_up(sizeof(TileMeta) * L.max_tiles);
     L.lookback0 = at;   at += align_up(sizeof(uint32_t) * RADIX * L.max_tiles);
     L.lookback1 = at;   at += align_up(sizeof(uint32_t) * RADIX * L.max_tiles);
     L.total = at;
@@ -890,6 +912,7 @@ rs_status run_segmented(rs_ctx* ctx, const void* keys_in, void* keys_out, const 
     a.tile_start = reinterpret_cast<uint32_t*>(T + L.tile_start);
     a.tile_owner = reinterpret_cast<uint32_t*>(T + L.tile_owner);
     a.long_tile = reinterpret_cast<uint32_t*>(T + L.long_tile);
+    a.tile_meta = reinterpret_cast<TileMeta*>(T + L.tile_meta);
     a.lookback[0] = reinterpret_cast<uint32_t*>(T + L.lookback0);
     a.lookback[1] = reinterpret_cast<uint32_t*>(T + L.lookback1);
     a.max_tiles = L.max_tiles;
