@@ -175,6 +175,14 @@ __device__ __forceinline__ void bulk_prefetch_l2(const void* p, uint32_t bytes) 
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
+// The whole 16-byte lines inside [p, p + bytes) prefetched into L2 (the
+// range's unaligned ends are left out, so nothing outside it is touched).
+__device__ __forceinline__ void prefetch_lines_l2(const void* p, uint64_t bytes) {
+    const uintptr_t b = ((uintptr_t)p + 15) & ~(uintptr_t)15;
+    const uintptr_t e = ((uintptr_t)p + bytes) & ~(uintptr_t)15;
+    if (e > b) bulk_prefetch_l2(reinterpret_cast<const void*>(b), (uint32_t)(e - b));
+}
+
 // Lanes of the warp holding the same 8-bit digit: one ballot per bit.  Per
 // bit b: p = bit set, sx = all ones when set, bal = lanes with the bit set,
 // and peers &= ~(bal ^ sx) in one lop3 (truth table 0x90 for a & ~(b ^ c)

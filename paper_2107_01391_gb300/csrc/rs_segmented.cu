@@ -109,6 +109,7 @@ struct SegArgs {
     uint32_t* tile_owner;  // [max_tiles] order index of the segment owning a tile
     uint32_t* long_tile;   // [max_tiles] the device tiles of segments of count_par_min keys or more
     TileMeta* tile_meta;   // [max_tiles]
+    uint32_t prefetch_ahead;  // device tiles between a tile and the one it prefetches
     uint32_t* lookback[2];
     uint64_t max_tiles;
     uint32_t n_large_max;  // room of bins, dev_use and tile_start
@@ -621,6 +622,39 @@ __global__ void __launch_bounds__(BLOCK, 2) seg_pass_kernel(SegArgs a, uint32_t 
         // the same words, so the tests are uniform
         const uint4 mw = __ldcg(reinterpret_cast<const uint4*>(&a.tile_meta[g]));
         const uint32_t slot = __ldcg(&a.tile_owner[g]);
+        // the tile claimed about half a residency later (tiles are claimed in
+        // order): the last thread reads its record in the same round trip and
+        // prefetches its keys and values into L2 (a TMA bulk prefetch of the
+        // whole 16-byte lines in range), so their loads do not wait on DRAM
+        const uint32_t pg = g + a.prefetch_ahead;
+        if (a.prefetch_ahead && t == BLOCK - 1 && pg < dev_tiles) {
+            const uint4 pm = __ldcg(reinterpret_cast<const uint4*>(&a.tile_meta[pg]));
+            const uint64_t plo = (uint64_t)pm.x | ((uint64_t)pm.y << 32);
+            const uint64_t plen = pm.z, ptb = (uint64_t)(pm.w & 0xffffffu) * TILE;
+            const uint32_t puse = pm.w >> 24;
+            if ((puse >> pass & 1u) && ptb < plen && plo + plen <= a.n) {
+                const uint64_t pvalid = min((uint64_t)TILE, plen - ptb);
+                const uint32_t pf_end = __popc(puse) - 1 - __popc(puse & ((1u << pass) - 1u));
+                const bool pfirst = (puse & ((1u << pass) - 1u)) == 0;
+                const uint32_t psrc = pfirst ? BUF_IN : (((pf_end + 1) & 1u) ? BUF_TMP : BUF_OUT);
+                const char* kp;
+                uint64_t kes = sizeof(Cell);
+                if (psrc == BUF_IN) {
+                    kp = static_cast<const char*>(a.keys_in) + (plo + ptb) * sizeof(In);
+                    kes = sizeof(In);
+                } else if (psrc == BUF_TMP) {
+                    kp = reinterpret_cast<const char*>(static_cast<const Cell*>(a.keys_tmp) + plo + ptb);
+                } else {
+                    kp = static_cast<const char*>(a.keys_out) + plo * sizeof(Out) + ptb * sizeof(Cell);
+                }
+                prefetch_lines_l2(kp, pvalid * kes);
+                if (kPairs && !(pfirst && a.iota)) {
+                    const VS* vb = static_cast<const VS*>(
+                        psrc == BUF_IN ? a.vals_in : (psrc == BUF_TMP ? a.vals_tmp : a.vals_out));
+                    prefetch_lines_l2(vb + plo + ptb, pvalid * sizeof(VS));
+                }
+            }
+        }
         const uint64_t lo = (uint64_t)mw.x | ((uint64_t)mw.y << 32);
         const uint64_t len = mw.z;
         const uint32_t lt = mw.w & 0xffffffu;  // tile index within the segment
@@ -989,6 +1023,7 @@ rs_status run_segmented(rs_ctx* ctx, const void* keys_in, void* keys_out, const 
             dps = occ;
         }
         const int dgrid = (int)std::min<size_t>((size_t)sms * dps, L.max_tiles);
+        a.prefetch_ahead = prefetch_ahead_for(dgrid);
         for (uint32_t p = 0; p < passes; p++) {
             LaunchTimer lt(ctx, KC_SEG, st);
             dkern<<<dgrid, BLOCK, DSmem::kBytes, st>>>(a, p);
