@@ -55,10 +55,11 @@ constexpr uint64_t WARP_SEG_MAX = 63;         // segments sorted by one warp
 constexpr uint64_t SEG_MAX_LEN = RS_MAX_N;  // look-back words of the device tier hold 30-bit counts
 // Segments of at least 2^DEV_MIN_LOG2 keys go to the device tier: exactly the
 // size classes 0..DEV_CLASS_MAX (class = leading zeros of the length).
-// Shorter ones above one tile are swept by one CTA.  2^14 measured best
-// (Run B / Run A / 8192-key rows, ms: 2^13 6.27 / 133.0 / 1.41, 2^14 6.12 /
-// 132.9 / 1.05, 2^15 6.21 / 133.0 / 1.04, 2^16 6.42 / 133.6 / 1.04).
-constexpr uint32_t DEV_MIN_LOG2 = 14;
+// Shorter ones above one tile are swept by one CTA.  With the device tier's
+// L2 prefetch, 2^13 measured best (Run B / Run A, ms: 2^13 5.64 / 115.8,
+// 2^14 5.70 / 115.4, 2^15 6.10 / 116.2); without it 2^14 was (2^13 6.27 /
+// 133.0, 2^14 6.12 / 132.9).
+constexpr uint32_t DEV_MIN_LOG2 = 13;
 constexpr uint32_t DEV_CLASS_MAX = 63 - DEV_MIN_LOG2;
 static_assert((1u << DEV_MIN_LOG2) > SEG_TILE, "the device tier starts above the on-chip tier");
 

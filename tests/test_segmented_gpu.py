@@ -24,7 +24,9 @@ def ctx(rs):
     c.close()
 
 
-SIZES = [0, 1, 2, 17, 31, 32, 33, 255, 256, 257, 1000, 4095, 4096, 4097, 5000, 12_289, 70_000, 3, 0]
+# around the tier boundaries: 63 (warp), 4096 (on chip), 8192 (device tier)
+SIZES = [0, 1, 2, 17, 31, 32, 33, 255, 256, 257, 1000, 4095, 4096, 4097, 5000, 8191, 8192, 8193,
+         12_289, 70_000, 3, 0]
 
 
 def _offsets(sizes):
