@@ -302,6 +302,20 @@ typedef struct rs_plan_info {
 } rs_plan_info;
 rs_status rs_ctx_last_plan(rs_ctx* ctx, rs_plan_info* info);
 
+/* Pass-tile selection (not in the paper; the paper sorts on one CPU).  The
+ * digit-group passes of rs_sort_u32, rs_sort_fixed_decimal (with at most 9
+ * digits) and rs_sort_pairs (4-byte cells with no value or a 4-byte value)
+ * come in two tile sizes: a wide tile (40-48 keys per thread, 2-3 CTAs per
+ * SM), fastest for large sorts, and a narrow one (16 keys per thread, 3 CTAs
+ * per SM) that spreads a sort of a few hundred thousand keys over more SMs.
+ * Sorts of more than 4096 keys and at most narrow_max_n keys take the narrow
+ * tile.  The default, 2^19, is the crossover measured on GB300;
+ * paper_2107_01391_gb300/tune.py measures it on the device at hand.  Both
+ * tiles give the same result; a workspace query covers either.
+ * RS_ERR_INVALID for a NULL context or output pointer. */
+rs_status rs_ctx_set_pass_tile_limit(rs_ctx* ctx, uint64_t narrow_max_n);
+rs_status rs_ctx_pass_tile_limit(rs_ctx* ctx, uint64_t* narrow_max_n);
+
 /* Per-kernel timing with CUDA events recorded on the launching stream around
  * every launch (off by default).  Kernel classes: "hist" (counting), "pass"
  * (digit-group passes), "fill" (rebuild from cells), "pack" (string alphabet

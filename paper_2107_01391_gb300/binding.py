@@ -34,7 +34,10 @@ RS_FILL_CELLS = 4096
 # Every function the header declares (the CPU test checks the export table).
 EXPORTS = ("rs_ctx_create", "rs_ctx_destroy", "rs_ctx_status", "rs_sort_u32", "rs_sort_u64",
            "rs_sort_fixed_decimal", "rs_sort_pairs", "rs_ctx_last_plan", "rs_ctx_set_timing",
-           "rs_ctx_kernel_time", "rs_ctx_reset_timing", "rs_ctx_launch_count", "rs_version")
+           "rs_ctx_kernel_time", "rs_ctx_reset_timing", "rs_ctx_launch_count", "rs_version",
+           "rs_sort_strings", "rs_sort_segmented", "rs_scatter_rows", "rs_traverse_maps",
+           "rs_sort_u32_noalloc", "rs_debug_wait_timeout", "rs_ctx_set_pass_tile_limit",
+           "rs_ctx_pass_tile_limit")
 
 
 class RsError(RuntimeError):
@@ -91,8 +94,11 @@ def lib() -> ctypes.CDLL:
         L.rs_traverse_maps.argtypes = [p, p, sz, ctypes.c_int, ctypes.c_int, ctypes.c_int, p, p,
                                        p, p, p, psz, p]
         L.rs_sort_u32_noalloc.argtypes = [p, p, sz, p, p]
+        L.rs_ctx_set_pass_tile_limit.argtypes = [p, ctypes.c_uint64]
+        L.rs_ctx_pass_tile_limit.argtypes = [p, ctypes.POINTER(ctypes.c_uint64)]
         for name in ("rs_sort_strings", "rs_sort_segmented", "rs_scatter_rows",
-                     "rs_traverse_maps", "rs_sort_u32_noalloc"):
+                     "rs_traverse_maps", "rs_sort_u32_noalloc", "rs_ctx_set_pass_tile_limit",
+                     "rs_ctx_pass_tile_limit"):
             getattr(L, name).restype = st
         for name in ("rs_ctx_create", "rs_ctx_destroy", "rs_ctx_status", "rs_ctx_last_plan",
                      "rs_ctx_set_timing", "rs_ctx_reset_timing", "rs_ctx_kernel_time",
@@ -161,14 +167,46 @@ class Context:
     def launch_count(self) -> int:
         return int(lib().rs_ctx_launch_count(self._h))
 
+    @property
+    def pass_tile_limit(self) -> int:
+        """Sorts of more than 4096 and at most this many keys take the narrow
+        pass tile (rs_ctx_set_pass_tile_limit)."""
+        v = ctypes.c_uint64()
+        _check(lib().rs_ctx_pass_tile_limit(self._h, ctypes.byref(v)), "rs_ctx_pass_tile_limit")
+        return int(v.value)
+
+    @pass_tile_limit.setter
+    def pass_tile_limit(self, narrow_max_n: int):
+        _check(lib().rs_ctx_set_pass_tile_limit(self._h, int(narrow_max_n)),
+               "rs_ctx_set_pass_tile_limit")
+
+    def apply_tuning(self, path: str | None = None) -> bool:
+        """Apply a tuning table written by ``paper_2107_01391_gb300.tune`` (the
+        file at ``path``, else $RS_TUNE_FILE) if it was measured on this
+        device's model; returns whether it was applied."""
+        import json
+        path = path or os.environ.get("RS_TUNE_FILE")
+        if not path or not os.path.exists(path):
+            return False
+        with open(path) as f:
+            table = json.load(f)
+        if table.get("device_name") != torch.cuda.get_device_name(self.device):
+            return False
+        self.pass_tile_limit = int(table["narrow_max_n"])
+        return True
+
 
 _default_ctx: dict[int, Context] = {}
 
 
 def default_context(device: int | None = None) -> Context:
+    """The per-device context the wrappers use when given none; a tuning table
+    named by $RS_TUNE_FILE is applied to it when created."""
     dev = torch.cuda.current_device() if device is None else int(device)
     if dev not in _default_ctx:
-        _default_ctx[dev] = Context(dev)
+        c = Context(dev)
+        c.apply_tuning()
+        _default_ctx[dev] = c
     return _default_ctx[dev]
 
 

@@ -167,6 +167,20 @@ rs_status rs_ctx_last_plan(rs_ctx* ctx, rs_plan_info* info) {
     return RS_OK;
 }
 
+rs_status rs_ctx_set_pass_tile_limit(rs_ctx* ctx, uint64_t narrow_max_n) {
+    if (!ctx) return RS_ERR_INVALID;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    ctx->narrow_max_n = narrow_max_n;
+    return RS_OK;
+}
+
+rs_status rs_ctx_pass_tile_limit(rs_ctx* ctx, uint64_t* narrow_max_n) {
+    if (!ctx || !narrow_max_n) return RS_ERR_INVALID;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    *narrow_max_n = ctx->narrow_max_n;
+    return RS_OK;
+}
+
 rs_status rs_ctx_set_timing(rs_ctx* ctx, int enable) {
     if (!ctx) return RS_ERR_INVALID;
     ctx->timing = enable != 0;

@@ -44,6 +44,10 @@ struct rs_ctx {
     uint64_t launches = 0;
     uint32_t last_passes_total = 0;
     uint32_t last_tiles = 0;
+    // sorts of at most this many keys take the narrow pass tile where one
+    // exists (rs_ctx_set_pass_tile_limit; the default is the measured
+    // crossover on GB300)
+    uint64_t narrow_max_n = (uint64_t)1 << 19;
     bool timing = false;
     std::vector<rs::TimedLaunch> timed[rs::KC_COUNT_];
     std::vector<cudaEvent_t> event_pool;

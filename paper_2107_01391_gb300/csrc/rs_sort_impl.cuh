@@ -91,16 +91,17 @@ inline int sm_count(int device) {
     return v;
 }
 
-// One sort: keys_in (C::In) -> keys_out (C::Out), values V (NoVal = keys only).
-// skip (device pointer, may be NULL): when it holds a non-zero word at run
-// time the whole sort is a no-op (used by callers that plan on the device).
-template <class C, typename V>
-rs_status run_sort(rs_ctx* ctx, const void* keys_in, void* keys_out, const void* vals_in,
-                   void* vals_out, size_t n, CodecParams prm, uint32_t cell_bits, void* temp,
-                   size_t* temp_bytes, cudaStream_t stream, const uint32_t* skip) {
+// One sort with pass tiles of PB * IPT keys: keys_in (C::In) -> keys_out
+// (C::Out), values V (NoVal = keys only).  skip (device pointer, may be
+// NULL): when it holds a non-zero word at run time the whole sort is a no-op
+// (used by callers that plan on the device).
+template <class C, typename V, int IPT>
+rs_status run_sort_tile(rs_ctx* ctx, const void* keys_in, void* keys_out, const void* vals_in,
+                        void* vals_out, size_t n, CodecParams prm, uint32_t cell_bits,
+                        void* temp, size_t* temp_bytes, cudaStream_t stream,
+                        const uint32_t* skip) {
     using Cell = typename C::Cell;
     constexpr bool kPairs = ValTraits<V>::kPairs;
-    constexpr int IPT = ipt_for<C, V>();
     constexpr int PB = pass_block<C, V>();
     constexpr int TILE = PB * IPT;
     const uint32_t passes = passes_for(cell_bits);
@@ -222,7 +223,7 @@ rs_status run_sort(rs_ctx* ctx, const void* keys_in, void* keys_out, const void*
             return RS_ERR_CUDA;
         smem_set[ctx->device].store(true, std::memory_order_release);
     }
-    const uint32_t ahead = prefetch_ahead_for(PassShape<C, V>::kCTAs * sm_count(ctx->device));
+    const uint32_t ahead = prefetch_ahead_for(pass_ctas<C, V, IPT, PB>() * sm_count(ctx->device));
     for (uint32_t p = 0; p < passes; p++) {
         PassArgs a{};
         a.keys_in = keys_in;
@@ -248,6 +249,36 @@ rs_status run_sort(rs_ctx* ctx, const void* keys_in, void* keys_out, const void*
     ctx->last_passes_total = passes;
     ctx->last_tiles = (uint32_t)L.tiles;
     return cudaGetLastError() == cudaSuccess ? RS_OK : RS_ERR_CUDA;
+}
+
+// One sort, choosing the pass tile: the narrow one (NarrowShape) for sorts
+// of more than one on-chip tile and at most ctx->narrow_max_n keys where the
+// shape has one, the wide one (PassShape) otherwise.  A workspace query
+// returns room for either, so it needs no context.
+template <class C, typename V>
+rs_status run_sort(rs_ctx* ctx, const void* keys_in, void* keys_out, const void* vals_in,
+                   void* vals_out, size_t n, CodecParams prm, uint32_t cell_bits, void* temp,
+                   size_t* temp_bytes, cudaStream_t stream, const uint32_t* skip) {
+    constexpr int WIDE = ipt_for<C, V>();
+    if constexpr (NarrowShape<C, V>::kHas) {
+        constexpr int NARROW = NarrowShape<C, V>::kIPT;
+        if (!temp && temp_bytes) {
+            size_t wide = 0, narrow = 0;
+            rs_status s = run_sort_tile<C, V, WIDE>(ctx, keys_in, keys_out, vals_in, vals_out, n,
+                                                    prm, cell_bits, nullptr, &wide, stream, skip);
+            if (s != RS_OK) return s;
+            s = run_sort_tile<C, V, NARROW>(ctx, keys_in, keys_out, vals_in, vals_out, n, prm,
+                                            cell_bits, nullptr, &narrow, stream, skip);
+            if (s != RS_OK) return s;
+            *temp_bytes = std::max(wide, narrow);
+            return RS_OK;
+        }
+        if (ctx && n > SMALL_TILE && n <= ctx->narrow_max_n)
+            return run_sort_tile<C, V, NARROW>(ctx, keys_in, keys_out, vals_in, vals_out, n, prm,
+                                               cell_bits, temp, temp_bytes, stream, skip);
+    }
+    return run_sort_tile<C, V, WIDE>(ctx, keys_in, keys_out, vals_in, vals_out, n, prm,
+                                     cell_bits, temp, temp_bytes, stream, skip);
 }
 
 #define RS_DECLARE_SORT(C, V)                                                                  \

@@ -120,9 +120,27 @@ def test_u64_keys(rs, ctx, oracle, n):
     assert np.array_equal(from_dev(out, np.uint64), ref)
 
 
+@pytest.fixture
+def wide_tiles(ctx):
+    """Every multi-tile sort on the wide pass tile (no narrow selection)."""
+    old = ctx.pass_tile_limit
+    ctx.pass_tile_limit = 0
+    yield
+    ctx.pass_tile_limit = old
+
+
+@pytest.fixture
+def narrow_tiles(ctx):
+    """Every multi-tile sort with a 4-byte cell on the narrow pass tile."""
+    old = ctx.pass_tile_limit
+    ctx.pass_tile_limit = 1 << 62
+    yield
+    ctx.pass_tile_limit = old
+
+
 @pytest.mark.parametrize("where", ["minus1", "exact", "plus1", "ragged3"])
 @pytest.mark.parametrize("shape", list(TILE_KEYS), ids=lambda s: f"{s[0]}-{s[1]}")
-def test_tile_boundaries(rs, ctx, oracle, shape, where):
+def test_tile_boundaries(rs, ctx, oracle, wide_tiles, shape, where):
     kt, vt = shape
     T = TILE_KEYS[shape]
     n = {"minus1": T - 1, "exact": T, "plus1": T + 1, "ragged3": 3 * T + 17}[where]
@@ -143,6 +161,62 @@ def test_tile_boundaries(rs, ctx, oracle, shape, where):
         assert np.array_equal(from_dev(ko, kdt), ref_k)
         assert np.array_equal(from_dev(vo, vdt), ref_v)
     assert ctx.last_plan()["tiles"] == -(-n // T)
+
+
+NARROW_TILE = 16 * 256
+
+
+@pytest.mark.parametrize("n", [4097, 2 * NARROW_TILE - 1, 2 * NARROW_TILE, 2 * NARROW_TILE + 1,
+                               5 * NARROW_TILE + 17, 1 << 19, (1 << 19) + 3])
+@pytest.mark.parametrize("kind", ["u32_keys", "u32_pairs", "f32_pairs", "dec_keys", "dec_pairs"])
+def test_narrow_tile_boundaries(rs, ctx, oracle, narrow_tiles, kind, n):
+    """The narrow pass tile (16 keys per thread) at its tile boundaries, for
+    every shape that has one, against the oracle."""
+    rng = np.random.default_rng(n + 7 * len(kind))
+    if kind.startswith("u32"):
+        keys = W.u32_keys(n, seed_extra=n)
+        keys[1::5] = keys[0::5][: keys[1::5].size]  # ties
+        ref_k, perm, _ = oracle.sort_u32(keys)
+        kdt = np.uint32
+    elif kind == "f32_pairs":
+        keys = np.round(rng.standard_normal(n) * 100).astype(np.float32)
+        _, perm, _ = oracle.sort_float(keys)
+        ref_k = keys[perm.astype(np.int64)]
+        ref_k[ref_k == 0] = 0.0
+        kdt = np.float32
+    else:
+        keys = W.decimals(n, 6, 3, seed_extra=n)
+        ref_k, perm, _ = oracle.sort_fixed_decimal(keys, 6, 3)
+        kdt = np.int64
+    if kind.endswith("keys"):
+        if kind == "u32_keys":
+            out = rs.rs_sort_u32(to_dev(keys), ctx=ctx)
+        else:
+            out = rs.rs_sort_fixed_decimal(to_dev(keys), 6, 3, ctx=ctx)
+        ctx.check()
+        assert np.array_equal(from_dev(out, kdt), ref_k)
+    else:
+        vals = np.arange(n, dtype=np.uint32)
+        ko, vo = rs.rs_sort_pairs(to_dev(keys), to_dev(vals),
+                                  decimal=(6, 3) if kind == "dec_pairs" else None, ctx=ctx)
+        ctx.check()
+        assert np.array_equal(from_dev(ko, kdt).view(np.uint8), ref_k.view(np.uint8))
+        assert np.array_equal(from_dev(vo, np.uint32), perm.astype(np.uint32))
+    assert ctx.last_plan()["tiles"] == -(-n // NARROW_TILE)
+
+
+def test_default_tile_selection(rs, ctx, oracle):
+    """With the default limit (2^19) a sort of 2^19 keys takes the narrow tile
+    and one of 2^19 + 1 the wide one; both agree with the oracle."""
+    assert ctx.pass_tile_limit == 1 << 19
+    for n, tile in ((1 << 19, NARROW_TILE), ((1 << 19) + 1, TILE_KEYS[("u32", "u32")])):
+        keys, vals = W.u32_pairs(n, "zipf", seed_extra=n)
+        ref_k, perm, _ = oracle.sort_u32(keys)
+        ko, vo = rs.rs_sort_pairs(to_dev(keys), to_dev(vals), ctx=ctx)
+        ctx.check()
+        assert np.array_equal(from_dev(ko, np.uint32), ref_k)
+        assert np.array_equal(from_dev(vo, np.uint32), perm.astype(np.uint32))
+        assert ctx.last_plan()["tiles"] == -(-n // tile)
 
 
 @pytest.mark.parametrize("n", [1, 2, 33, 1000, 4095, 4096])
