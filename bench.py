@@ -670,7 +670,7 @@ def configs_leg(binding, ctx, steps: int, warmup: int, hbm_peak: float):
     return out
 
 
-def autograd_leg(steps: int, warmup: int):
+def autograd_leg(steps: int, warmup: int, hbm_peak: float | None = None):
     """Differentiable row sort: 4096 x 8192 float32 rows of distinct keys,
     forward (sorted values + stable permutation) and backward (gradient
     scatter), timed separately with CUDA events."""
@@ -700,11 +700,19 @@ def autograd_leg(steps: int, warmup: int):
     n = x.numel()
     fwd /= steps
     bwd /= steps
+    # forward reads the key (4 B) and writes the sorted value (4 B) and its
+    # int64 index (8 B); backward reads g (4 B) and perm (8 B) and writes
+    # grad_x (4 B) per element
+    fwd_gbs = 16 * n / (fwd * 1e-3) / 1e9
+    bwd_gbs = 16 * n / (bwd * 1e-3) / 1e9
     return {"workload": "4096 x 8192 float32 rows of distinct keys (autograd.Function)",
             "forward_ms": fwd, "forward_keys_per_s": n / (fwd * 1e-3),
+            "forward_alg_bytes_per_key": 16, "forward_alg_gbs": fwd_gbs,
+            "forward_frac_of_measured_hbm": fwd_gbs / hbm_peak if hbm_peak else None,
+            "forward_kernel": "tile_rows_kernel<CodecF32, u64, 32, u32> (one launch)",
             "backward_ms": bwd,
-            # backward reads g (4 B) and perm (8 B) and writes grad_x (4 B) per element
-            "backward_gbs": 16 * n / (bwd * 1e-3) / 1e9}
+            "backward_gbs": bwd_gbs,
+            "backward_frac_of_measured_hbm": bwd_gbs / hbm_peak if hbm_peak else None}
 
 
 def library_context(steps: int, warmup: int):
@@ -982,7 +990,7 @@ def run_ours(args):
 
     agl = None
     if not args.no_autograd and world == 1:
-        agl = autograd_leg(max(1, min(args.steps, 10)), max(1, min(args.warmup, 3)))
+        agl = autograd_leg(max(1, min(args.steps, 10)), max(1, min(args.warmup, 3)), hbm_peak)
 
     cfgs = None
     if not args.no_configs and world == 1:
