@@ -180,37 +180,58 @@ __global__ void __launch_bounds__(BLOCK) seg_size_kernel(SegArgs a) {
 
 // Device tiles for the large segments (order[0 .. n_large)): each takes a
 // contiguous range of ceil(len / dev_tile) tiles from a shared counter, and
-// every tile records its owner.  Ranges come out in any order; within a
-// segment the tiles are in input order.
+// every tile records its owner and description.  Ranges come out in any
+// order; within a segment the tiles are in input order.  Each lane claims
+// the range of one segment, then the warp writes the entries of its 32
+// segments one segment at a time, 32 tiles per step, so that a single long
+// segment (an argsort of one array has 2^28 / dev_tile tiles) is not written
+// by one thread.
 __global__ void __launch_bounds__(BLOCK) seg_tiles_kernel(SegArgs a) {
     const uint32_t n_large = __ldcg(&a.ctl->n_large);
-    for (uint64_t i = (uint64_t)blockIdx.x * BLOCK + threadIdx.x; i < n_large;
-         i += (uint64_t)gridDim.x * BLOCK) {
-        uint64_t lo, hi;
-        seg_bounds(a, a.order[i], lo, hi);  // valid: bad bounds are in the last class
-        const uint32_t tiles = (uint32_t)((hi - lo + a.dev_tile - 1) / a.dev_tile);
-        const uint32_t start = atomicAdd(&a.ctl->dev_tiles, tiles);
-        if ((uint64_t)start + tiles > a.max_tiles) {  // cannot happen: the host's bound
-            atomicOr(a.status, STATUS_RANGE);
-            a.tile_start[i] = 0xffffffffu;
-            continue;
+    const uint32_t lane = lane_id();
+    for (uint64_t base = (uint64_t)blockIdx.x * BLOCK + (threadIdx.x & ~31u); base < n_large;
+         base += (uint64_t)gridDim.x * BLOCK) {
+        const uint64_t i = base + lane;
+        uint64_t lo = 0, hi = 0;
+        uint32_t tiles = 0, start = 0;
+        if (i < n_large) {
+            seg_bounds(a, a.order[i], lo, hi);  // valid: bad bounds are in the last class
+            tiles = (uint32_t)((hi - lo + a.dev_tile - 1) / a.dev_tile);
+            start = atomicAdd(&a.ctl->dev_tiles, tiles);
+            if ((uint64_t)start + tiles > a.max_tiles) {  // cannot happen: the host's bound
+                atomicOr(a.status, STATUS_RANGE);
+                a.tile_start[i] = 0xffffffffu;
+                tiles = 0;
+            } else {
+                a.tile_start[i] = start;
+            }
         }
-        a.tile_start[i] = start;
-        for (uint32_t j = 0; j < tiles; j++) {
-            a.tile_owner[start + j] = (uint32_t)i;
-            TileMeta m;
-            m.lo = lo;
-            m.len = (uint32_t)(hi - lo);
-            m.lt_use = j;  // the moving groups are added when the segment is counted
-            a.tile_meta[start + j] = m;
-        }
-        // a long segment's tiles are listed for seg_count_kernel, which adds
-        // their counts into the segment's rows of bins: they start at zero
-        if (hi - lo >= a.count_par_min) {
-            const uint32_t ls = atomicAdd(&a.ctl->long_tiles, tiles);  // <= dev_tiles
-            for (uint32_t j = 0; j < tiles; j++) a.long_tile[ls + j] = start + j;
-            for (uint32_t w = 0; w < a.passes * RADIX; w++)
-                a.bins[(uint64_t)i * a.passes * RADIX + w] = 0;
+        for (int src = 0; src < 32; src++) {
+            const uint32_t st = __shfl_sync(0xffffffffu, tiles, src);
+            if (st == 0) continue;  // warp-uniform
+            const uint32_t s0 = __shfl_sync(0xffffffffu, start, src);
+            const uint64_t slo = __shfl_sync(0xffffffffu, lo, src);
+            const uint64_t shi = __shfl_sync(0xffffffffu, hi, src);
+            const uint32_t owner = (uint32_t)(base + src);
+            for (uint32_t j = lane; j < st; j += 32) {
+                a.tile_owner[s0 + j] = owner;
+                TileMeta m;
+                m.lo = slo;
+                m.len = (uint32_t)(shi - slo);
+                m.lt_use = j;  // the moving groups are added when the segment is counted
+                a.tile_meta[s0 + j] = m;
+            }
+            // a long segment's tiles are listed for seg_count_kernel, which
+            // adds their counts into the segment's rows of bins: they start
+            // at zero
+            if (shi - slo >= a.count_par_min) {
+                uint32_t ls = 0;
+                if (lane == 0) ls = atomicAdd(&a.ctl->long_tiles, st);  // <= dev_tiles
+                ls = __shfl_sync(0xffffffffu, ls, 0);
+                for (uint32_t j = lane; j < st; j += 32) a.long_tile[ls + j] = s0 + j;
+                for (uint32_t w = lane; w < a.passes * RADIX; w += 32)
+                    a.bins[(uint64_t)owner * a.passes * RADIX + w] = 0;
+            }
         }
     }
 }
@@ -226,7 +247,9 @@ template <class C>
 __global__ void __launch_bounds__(BLOCK) seg_count_kernel(SegArgs a) {
     using Cell = typename C::Cell;
     using In = typename C::In;
+    constexpr int U = 8;  // loads in flight per thread
     __shared__ uint32_t sh[MAX_PASSES][RADIX];
+    __shared__ uint32_t s_slot;
     const uint32_t t = threadIdx.x;
     const uint32_t n_large = __ldcg(&a.ctl->n_large);
     const uint32_t dev_tiles = (uint32_t)min((uint64_t)__ldcg(&a.ctl->dev_tiles), a.max_tiles);
@@ -234,39 +257,59 @@ __global__ void __launch_bounds__(BLOCK) seg_count_kernel(SegArgs a) {
     const uint32_t words = a.passes * RADIX;
     const In* kin = static_cast<const In*>(a.keys_in);
     bool ok = true;
+    // The counts of consecutive tiles of one segment (a CTA's tiles k, k+G,
+    // ... of the list mostly share their segment) add up in shared memory
+    // and reach the segment's rows in global memory once per segment.
+    for (uint32_t i = t; i < words; i += BLOCK) (&sh[0][0])[i] = 0;
+    if (t == 0) s_slot = 0xffffffffu;
+    __syncthreads();
+    auto flush = [&]() {
+        const uint32_t cur = s_slot;
+        if (cur != 0xffffffffu) {
+            uint32_t* row = a.bins + (uint64_t)cur * words;
+            for (uint32_t i = t; i < words; i += BLOCK) {
+                const uint32_t v = (&sh[0][0])[i];
+                if (v) atomicAdd(&row[i], v);
+                (&sh[0][0])[i] = 0;
+            }
+        }
+    };
     for (uint32_t k = blockIdx.x; k < long_tiles; k += gridDim.x) {
         const uint32_t g = a.long_tile[k];
         if (g >= dev_tiles) continue;  // cannot happen: written by seg_tiles_kernel
-        // the owner, checked as seg_pass_kernel checks it (uniform per CTA)
-        const uint32_t slot = a.tile_owner[g];
-        uint64_t lo = 0, hi = 0;
-        uint32_t first_tile = 0;
-        bool own = slot < n_large;
-        if (own) {
-            first_tile = a.tile_start[slot];
-            own = seg_bounds(a, a.order[slot], lo, hi) && first_tile != 0xffffffffu &&
-                  g >= first_tile && (uint64_t)(g - first_tile) * a.dev_tile < hi - lo &&
-                  hi - lo >= a.count_par_min;
+        // the tile's description and owner (uniform per CTA)
+        const uint4 mw = __ldcg(reinterpret_cast<const uint4*>(&a.tile_meta[g]));
+        const uint32_t slot = __ldcg(&a.tile_owner[g]);
+        const uint64_t lo = (uint64_t)mw.x | ((uint64_t)mw.y << 32);
+        const uint64_t len = mw.z;
+        const uint64_t tb = (uint64_t)(mw.w & 0xffffffu) * a.dev_tile;
+        if (!(slot < n_large && tb < len && lo + len <= a.n && len >= a.count_par_min)) continue;
+        if (slot != s_slot) {  // uniform: every thread read s_slot after the last barrier
+            flush();
+            __syncthreads();
+            if (t == 0) s_slot = slot;
         }
-        if (!own) continue;
-        for (uint32_t i = t; i < words; i += BLOCK) (&sh[0][0])[i] = 0;
-        __syncthreads();
-        const uint64_t base = lo + (uint64_t)(g - first_tile) * a.dev_tile;
-        const uint64_t end = min(hi, base + a.dev_tile);
-        for (uint64_t j = base + t; j < end; j += BLOCK) {
-            const Cell c = C::decode(kin[j], a.prm, ok);
+        const uint64_t base = lo + tb;
+        const uint64_t end = min(lo + len, base + a.dev_tile);
+        for (uint64_t j = base + t; j < end; j += (uint64_t)U * BLOCK) {
+            In kv[U];
 #pragma unroll
-            for (uint32_t p = 0; p < sizeof(Cell); p++)
-                if (p < a.passes) atomicAdd(&sh[p][digit_of(c, p * RADIX_BITS)], 1u);
+            for (int u = 0; u < U; u++) {
+                const uint64_t idx = j + (uint64_t)u * BLOCK;
+                kv[u] = idx < end ? __ldcs(&kin[idx]) : In(0);
+            }
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                if (j + (uint64_t)u * BLOCK >= end) break;
+                const Cell c = C::decode(kv[u], a.prm, ok);
+#pragma unroll
+                for (uint32_t p = 0; p < sizeof(Cell); p++)
+                    if (p < a.passes) atomicAdd(&sh[p][digit_of(c, p * RADIX_BITS)], 1u);
+            }
         }
-        __syncthreads();
-        uint32_t* row = a.bins + (uint64_t)slot * words;
-        for (uint32_t i = t; i < words; i += BLOCK) {
-            const uint32_t v = (&sh[0][0])[i];
-            if (v) atomicAdd(&row[i], v);
-        }
-        __syncthreads();  // sh is cleared for the next tile
+        __syncthreads();  // this tile's counts are in, and s_slot is set
     }
+    flush();
     if (!ok) atomicOr(a.status, STATUS_RANGE);
 }
 
