@@ -408,14 +408,17 @@ def _batched_segmented(binding, ctx, dk, dv, doff, ko, vo, steps, warmup, stream
     return e0.elapsed_time(e1) / steps, (ctx.launch_count() - launches0) / steps
 
 
-SEG_ONCHIP_KEYS = 4096  # segments up to one on-chip tile are read once and written once
+# segments below the device tier (2^13 keys) are sorted on chip, read once and
+# written once: by one warp, one on-chip tile, or the row tier's 8192-key tile
+SEG_ONCHIP_KEYS = (1 << 13) - 1
 
 
 def seg_alg_bytes(sizes: np.ndarray, passes: int = 4) -> int:
-    """Algorithmic bytes of a segmented u32-key + 4-byte-value sort: the warp
-    and on-chip tiers move each pair once (8 B in, 8 B out); a larger segment
-    reads its keys once to count (4 B) and moves every pair once per active
-    digit group (16 B each; all four are active for uniform keys)."""
+    """Algorithmic bytes of a segmented u32-key + 4-byte-value sort: the warp,
+    on-chip and row tiers move each pair once (8 B in, 8 B out); a segment of
+    the device tier reads its keys once to count (4 B) and moves every pair
+    once per active digit group (16 B each; all four are active for uniform
+    keys)."""
     small = int(sizes[sizes <= SEG_ONCHIP_KEYS].sum())
     large = int(sizes[sizes > SEG_ONCHIP_KEYS].sum())
     return 16 * small + (4 + 16 * passes) * large

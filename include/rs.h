@@ -200,7 +200,9 @@ rs_status rs_sort_strings(rs_ctx* ctx, const uint8_t* chars, const uint32_t* off
  * their output is unspecified).  The segments are sorted largest first by
  * one persistent launch: those of at most 63 keys by one warp each, of at
  * most 4096 keys on chip by one CTA in one read and one write, below 2^13
- * keys by one CTA each; longer ones by device-wide passes over all of them
+ * keys by one CTA each (whole on chip in one read and one write for 4-byte
+ * keys with no value, a 4-byte value or an argsort; tile by tile for other
+ * shapes); longer ones by device-wide passes over all of them
  * at once, one launch per digit group, with a look-back per segment.  A
  * segment longer than one CTA's share of the batch (such as the single
  * segment of an argsort of one array) is counted tile-parallel first, so

@@ -118,6 +118,10 @@ struct SegArgs {
     // device-tier segments of at least this many keys are counted tile by
     // tile by seg_count_kernel; shorter ones by the CTA that takes them
     uint64_t count_par_min;
+    // segments of SEG_TILE+1 .. ROW_TILE-1 keys are sorted whole on chip by
+    // seg_rows_kernel (4-byte cells with no value, a 4-byte value or an
+    // argsort); seg_sort_kernel leaves them out
+    uint32_t row_tier;
 };
 
 // Size class: 0 holds the largest segments (2^63 and up), 63 the empty ones.
@@ -458,6 +462,7 @@ __global__ void __launch_bounds__(BLOCK, seg_ctas_per_sm<C, V>()) seg_sort_kerne
         Cell k[SEG_IPT];
         VS v[SEG_IPT];
         const bool device_tier = first_w < __ldcg(&a.ctl->n_large);
+        if (a.row_tier && !device_tier && len > SEG_TILE && len < ROW_TILE) continue;
         if (!device_tier && len <= SEG_TILE) {
             // ---- one tile: sorted on chip, read once and written once ----
             const uint32_t valid = (uint32_t)len;
@@ -615,6 +620,46 @@ __global__ void __launch_bounds__(BLOCK, seg_ctas_per_sm<C, V>()) seg_sort_kerne
             src_buf = dst_buf;
             done++;
         }
+    }
+}
+
+// The row tier: segments of SEG_TILE+1 .. ROW_TILE-1 keys, which are exactly
+// the size class of lengths 2^12 .. 2^13-1 of the ordered list (less those of
+// 2^12 keys, which seg_sort_kernel keeps on chip), each sorted whole on chip
+// by one CTA as the row kernel sorts an equal row: 32 keys per thread, one
+// read, a rank per non-trivial digit group, one write (16 bytes per key and
+// value instead of the sweep's 4 + 16 per digit group).  A row shorter than
+// the tile is padded and ranked as a whole tile, with no position tests.
+constexpr uint32_t ROW_CLASS = 63 - 12;  // leading zeros of 2^12 .. 2^13-1
+static_assert(SEG_TILE == (1u << 12) && ROW_TILE == (1u << 13) && DEV_MIN_LOG2 == 13,
+              "the row tier is one size class between the on-chip and device tiers");
+
+template <class C, typename V, typename VR>
+__global__ void __launch_bounds__(BLOCK, 2) seg_rows_kernel(SegArgs a) {
+    using Cell = typename C::Cell;
+    constexpr bool kPairs = ValTraits<V>::kPairs;
+    using VS = typename std::conditional<kPairs, VR, uint32_t>::type;
+    __shared__ TileShared ts;
+    __shared__ Cell s_ref;
+    extern __shared__ __align__(16) unsigned char smem_dyn[];
+    const Stage<Cell, VS, kPairs, ROW_TILE> stage{smem_dyn};
+    const uint32_t end = __ldcg(&a.ctl->class_cursor[ROW_CLASS]);
+    const uint32_t begin = end - __ldcg(&a.ctl->class_count[ROW_CLASS]);
+    RowsArgs ra{};
+    ra.keys_in = a.keys_in;
+    ra.keys_out = a.keys_out;
+    ra.vals_in = a.vals_in;
+    ra.vals_out = a.vals_out;
+    ra.iota = a.iota;
+    ra.passes = a.passes;
+    ra.prm = a.prm;
+    ra.status = a.status;
+    for (uint32_t r = begin + blockIdx.x; r < end; r += gridDim.x) {
+        uint64_t lo, hi;
+        if (!seg_bounds(a, a.order[r], lo, hi)) continue;  // (uniform per CTA)
+        const uint64_t len = hi - lo;
+        if (len <= SEG_TILE || len >= ROW_TILE) continue;
+        sort_row<C, V, ROW_IPT, VR, true, false>(ra, lo, (uint32_t)len, ts, s_ref, stage);
     }
 }
 
@@ -996,6 +1041,10 @@ rs_status run_segmented(rs_ctx* ctx, const void* keys_in, void* keys_out, const 
     a.max_tiles = L.max_tiles;
     a.n_large_max = (uint32_t)L.n_large_max;
     a.dev_tile = DTILE;
+    // the row tier holds 32 keys and 32 four-byte values per thread: 4-byte
+    // cells with no value, a 4-byte value, or an argsort (indices carried as
+    // 32-bit words)
+    a.row_tier = sizeof(Cell) == 4 && (!kPairs || sizeof(VS) == 4 || iota);
     const int sms = sm_count(ctx->device);
     const size_t smem = sizeof(Cell) * SEG_TILE + (kPairs ? sizeof(VS) * SEG_TILE : 0);
     auto kern = seg_sort_kernel<C, V>;
@@ -1043,6 +1092,23 @@ rs_status run_segmented(rs_ctx* ctx, const void* keys_in, void* keys_out, const 
     {
         LaunchTimer lt(ctx, KC_SEG, st);
         kern<<<grid, BLOCK, smem, st>>>(a);
+    }
+    if constexpr (sizeof(Cell) == 4) {
+      if (a.row_tier) {
+        // (an argsort's indices travel as 32-bit words, as in the row path)
+        using VR = typename std::conditional<kPairs && sizeof(VS) == 8, uint32_t, VS>::type;
+        auto rkern = seg_rows_kernel<C, V, VR>;
+        const size_t rsmem = (size_t)ROW_TILE * (sizeof(Cell) + (kPairs ? sizeof(VR) : 0));
+        static std::atomic<bool> rsmem_set[64];  // zero-initialised: false
+        if (ctx->device < 64 && !rsmem_set[ctx->device].load(std::memory_order_acquire)) {
+            if (cudaFuncSetAttribute(rkern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)rsmem) != cudaSuccess)
+                return RS_ERR_CUDA;
+            rsmem_set[ctx->device].store(true, std::memory_order_release);
+        }
+        LaunchTimer lt(ctx, KC_SEG, st);
+        rkern<<<sms * 2, BLOCK, rsmem, st>>>(a);
+      }
     }
     if (L.n_large_max) {
         // the device tier: one launch per digit group over all large segments

@@ -118,10 +118,16 @@ struct RowsArgs {
     const uint32_t* skip;  // nullable; non-zero at run time: the sort is a no-op
 };
 
-// One row: load, one rank per non-trivial digit group, write.  kFull: the
-// row fills the tile (n == BLOCK * IPT), so no position is tested.
-template <class C, typename V, int IPT, typename VR, bool kFull>
-__device__ __forceinline__ uint32_t sort_row(const RowsArgs& a, uint64_t row, TileShared& ts,
+// One row of n keys starting at key `base`: load, one rank per non-trivial
+// digit group, write.  kCheckIO: loads and stores test the position (n may
+// be below BLOCK * IPT).  kCheckRank: the ranks test it too; without it a
+// short row is ranked as a whole tile whose positions from n on hold padding
+// keys of the largest cell, which start after every real key and so stay in
+// the tile's last positions through every stable group (the trivial-group
+// test looks at the real keys only).
+template <class C, typename V, int IPT, typename VR, bool kCheckIO, bool kCheckRank>
+__device__ __forceinline__ uint32_t sort_row(const RowsArgs& a, uint64_t base, uint32_t n,
+                                             TileShared& ts,
                                              typename C::Cell& s_ref,
                                              const Stage<typename C::Cell,
                                                          typename std::conditional<
@@ -137,10 +143,9 @@ __device__ __forceinline__ uint32_t sort_row(const RowsArgs& a, uint64_t row, Ti
     using VM = typename std::conditional<kPairs, V, uint32_t>::type;
     // the table match where the 32-key rows leave room for its constants
     constexpr bool kLut = IPT == ROW_IPT && sizeof(Cell) == 4 && sizeof(VS) == 4;
+    constexpr uint32_t TILE = BLOCK * IPT;
     const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
     const uint32_t w0 = warp * 32 * IPT + lane;  // warp-striped: input order
-    const uint32_t n = a.len;
-    const uint64_t base = row * n;
     Cell k[IPT];
     VS v[IPT];
     bool ok = true;
@@ -149,7 +154,7 @@ __device__ __forceinline__ uint32_t sort_row(const RowsArgs& a, uint64_t row, Ti
         const uint32_t j = w0 + i * 32;
         k[i] = ~Cell(0);
         v[i] = VS(0);
-        if (kFull || j < n) {
+        if (!kCheckIO || j < n) {
             k[i] = C::decode(static_cast<const In*>(a.keys_in)[base + j], a.prm, ok);
             if constexpr (kPairs)
                 v[i] = a.iota ? (VS)j : (VS) static_cast<const VM*>(a.vals_in)[base + j];
@@ -165,21 +170,22 @@ __device__ __forceinline__ uint32_t sort_row(const RowsArgs& a, uint64_t row, Ti
         bool same = true;
 #pragma unroll
         for (int i = 0; i < IPT; i++)
-            if (kFull || w0 + i * 32 < n) same &= digit_of(k[i], shift) == digit_of(ref, shift);
+            if (!kCheckIO || w0 + i * 32 < n) same &= digit_of(k[i], shift) == digit_of(ref, shift);
         if (__syncthreads_and(same)) continue;  // every key in one cell
         moved++;
-        rank_scatter<Cell, VS, IPT, kPairs, kLut, kFull>(k, v, n, shift, ts, stage);
+        rank_scatter<Cell, VS, IPT, kPairs, kLut, !kCheckRank>(k, v, kCheckRank ? n : TILE, shift,
+                                                              ts, stage);
 #pragma unroll
         for (int i = 0; i < IPT; i++) {
             const uint32_t j = w0 + i * 32;
-            if (kFull || j < n) stage.get(j, k[i], v[i]);
+            if (!kCheckRank || j < n) stage.get(j, k[i], v[i]);
         }
         __syncthreads();  // the staged tile is rewritten by the next group
     }
 #pragma unroll
     for (int i = 0; i < IPT; i++) {
         const uint32_t j = w0 + i * 32;
-        if (kFull || j < n) {
+        if (!kCheckIO || j < n) {
             static_cast<Out*>(a.keys_out)[base + j] = C::encode(k[i], a.prm);
             if constexpr (kPairs) static_cast<VM*>(a.vals_out)[base + j] = (VM)v[i];
         }
@@ -222,9 +228,9 @@ __global__ void __launch_bounds__(BLOCK, 2) tile_rows_kernel(RowsArgs a) {
             }
         }
         if (n == TILE)
-            moved = sort_row<C, V, IPT, VR, true>(a, row, ts, s_ref, stage);
+            moved = sort_row<C, V, IPT, VR, false, false>(a, row * n, n, ts, s_ref, stage);
         else
-            moved = sort_row<C, V, IPT, VR, false>(a, row, ts, s_ref, stage);
+            moved = sort_row<C, V, IPT, VR, true, true>(a, row * n, n, ts, s_ref, stage);
     }
     if (a.info && blockIdx.x == 0 && threadIdx.x == 0) {
         a.info->mode = MODE_PASSES;
