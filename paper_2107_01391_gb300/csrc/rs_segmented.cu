@@ -501,11 +501,23 @@ __global__ void __launch_bounds__(BLOCK, seg_ctas_per_sm<C, V>()) seg_sort_kerne
             __syncthreads();
             bool ok = true;
             const In* kin = static_cast<const In*>(a.keys_in);
-            for (uint64_t j = lo + t; j < hi; j += BLOCK) {
-                const Cell c = C::decode(kin[j], a.prm, ok);
+            // eight loads in flight per thread
+            constexpr int U = 8;
+            for (uint64_t j = lo + t; j < hi; j += (uint64_t)U * BLOCK) {
+                In kv[U];
 #pragma unroll
-                for (uint32_t p = 0; p < sizeof(Cell); p++)
-                    if (p < a.passes) atomicAdd(&s_hist[p][digit_of(c, p * RADIX_BITS)], 1u);
+                for (int u = 0; u < U; u++) {
+                    const uint64_t idx = j + (uint64_t)u * BLOCK;
+                    kv[u] = idx < hi ? __ldcs(&kin[idx]) : In(0);
+                }
+#pragma unroll
+                for (int u = 0; u < U; u++) {
+                    if (j + (uint64_t)u * BLOCK >= hi) break;
+                    const Cell c = C::decode(kv[u], a.prm, ok);
+#pragma unroll
+                    for (uint32_t p = 0; p < sizeof(Cell); p++)
+                        if (p < a.passes) atomicAdd(&s_hist[p][digit_of(c, p * RADIX_BITS)], 1u);
+                }
             }
             if (!ok) atomicOr(a.status, STATUS_RANGE);
         }
