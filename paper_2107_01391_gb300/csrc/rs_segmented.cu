@@ -1154,6 +1154,60 @@ rs_status run_segmented(rs_ctx* ctx, const void* keys_in, void* keys_out, const 
     return cudaGetLastError() == cudaSuccess ? RS_OK : RS_ERR_CUDA;
 }
 
+// Widen an argsort's 32-bit indices into the caller's 64-bit output: the
+// positions inside segments, [offsets[0], offsets[num_segs]) (offsets do not
+// decrease), or all n for equal segments; the others stay unwritten.
+__global__ void __launch_bounds__(BLOCK) widen_indices_kernel(const uint32_t* in, uint64_t* out,
+                                                              const uint64_t* seg_offsets,
+                                                              uint64_t num_segs, uint64_t n) {
+    uint64_t lo = 0, hi = n;
+    if (seg_offsets) {
+        lo = seg_offsets[0];
+        hi = min(seg_offsets[num_segs], n);
+    }
+    for (uint64_t j = lo + (uint64_t)blockIdx.x * BLOCK + threadIdx.x; j < hi;
+         j += (uint64_t)gridDim.x * BLOCK)
+        out[j] = in[j];
+}
+
+// An argsort with 8-byte indices outside the row path carries the indices as
+// 32-bit words (a segment holds fewer than 2^30 keys): every digit pass moves
+// 4 fewer bytes in and out per key, and one widening pass writes the 8-byte
+// output at the end.  Workspace: the 32-bit sort's, then n 32-bit indices.
+template <class C>
+rs_status run_segmented_argsort64(rs_ctx* ctx, const void* keys_in, void* keys_out,
+                                  void* vals_out, size_t n, const uint64_t* seg_offsets,
+                                  size_t num_segs, CodecParams prm, uint32_t cell_bits,
+                                  void* temp, size_t* temp_bytes, cudaStream_t st) {
+    size_t inner = 0;
+    rs_status s = run_segmented<C, uint32_t>(ctx, keys_in, keys_out, nullptr, nullptr, n,
+                                             seg_offsets, num_segs, prm, cell_bits, nullptr,
+                                             &inner, st, true);
+    if (s != RS_OK) return s;
+    const size_t idx_off = align_up(inner);
+    const size_t total = idx_off + align_up(sizeof(uint32_t) * std::max<size_t>(n, 1));
+    if (!temp) {
+        *temp_bytes = total;
+        return RS_OK;
+    }
+    if (*temp_bytes < total) return RS_ERR_TEMP_TOO_SMALL;
+    if (reinterpret_cast<uintptr_t>(temp) % 256) return RS_ERR_INVALID;
+    if (num_segs == 0 || n == 0) return RS_OK;
+    uint32_t* idx32 = reinterpret_cast<uint32_t*>(static_cast<unsigned char*>(temp) + idx_off);
+    size_t tb = inner;
+    s = run_segmented<C, uint32_t>(ctx, keys_in, keys_out, nullptr, idx32, n, seg_offsets,
+                                   num_segs, prm, cell_bits, temp, &tb, st, true);
+    if (s != RS_OK) return s;
+    DeviceGuard dg(ctx->device);
+    if (!dg.ok) return RS_ERR_CUDA;
+    const int grid = (int)std::max<size_t>(
+        1, std::min<size_t>((n + BLOCK - 1) / BLOCK, (size_t)sm_count(ctx->device) * 8));
+    LaunchTimer lt(ctx, KC_SEG, st);
+    widen_indices_kernel<<<grid, BLOCK, 0, st>>>(idx32, static_cast<uint64_t*>(vals_out),
+                                                 seg_offsets, num_segs, n);
+    return cudaGetLastError() == cudaSuccess ? RS_OK : RS_ERR_CUDA;
+}
+
 }  // namespace
 }  // namespace rs
 
@@ -1200,6 +1254,12 @@ extern "C" rs_status rs_sort_segmented(rs_ctx* ctx, rs_key_type kt, const void* 
         while (bits < 64 && ((2 * prm.bias) >> bits) != 0) bits++;
     }
     rs_status s;
+    // an argsort to 8-byte indices that the row path does not take carries
+    // 32-bit indices (run_segmented_argsort64); the row path carries them as
+    // 32-bit words already
+    const bool row_path = !seg_offsets && num_segs > 0 && n / num_segs > WARP_SEG_MAX &&
+                          n / num_segs <= ROW_TILE;
+    const bool argsort32 = iota && val_bytes == 8 && !row_path;
 #define RS_SEG_CALL(CODEC)                                                                      \
     do {                                                                                        \
         if (!pairs)                                                                             \
@@ -1210,6 +1270,9 @@ extern "C" rs_status rs_sort_segmented(rs_ctx* ctx, rs_key_type kt, const void* 
             s = run_segmented<CODEC, uint32_t>(ctx, keys_in, keys_out, vals_in, vals_out, n,    \
                                                seg_offsets, num_segs, prm, bits, temp,          \
                                                temp_bytes, st, iota);                           \
+        else if (argsort32)                                                                     \
+            s = run_segmented_argsort64<CODEC>(ctx, keys_in, keys_out, vals_out, n, seg_offsets,  \
+                                               num_segs, prm, bits, temp, temp_bytes, st);      \
         else                                                                                    \
             s = run_segmented<CODEC, uint64_t>(ctx, keys_in, keys_out, vals_in, vals_out, n,    \
                                                seg_offsets, num_segs, prm, bits, temp,          \

@@ -322,3 +322,32 @@ def test_run_b_full_size(rs, ctx):
         rk, rp, _ = O.sort_u32(keys[lo:hi])
         assert np.array_equal(ko_h[lo:hi], rk)
         assert np.array_equal(vo_h[lo:hi].astype(np.int64), lo + rp.astype(np.int64))
+
+
+@pytest.mark.parametrize("index_dtype", [torch.int64, torch.int32])
+@pytest.mark.parametrize("sizes", [[5, 9000, 300], [20_000], [100, 5000, 70_000, 0, 17]])
+def test_argsort_leaves_positions_outside_segments(rs, ctx, oracle, index_dtype, sizes):
+    """Segments that start after position 0 and end before n: the keys and
+    indices at positions outside every segment keep what the caller put
+    there, and each segment's indices (8-byte ones carried as 32-bit words
+    and widened at the end) are the oracle's."""
+    rng = np.random.default_rng(len(sizes) + sum(sizes))
+    head, tail = 37, 53
+    off = _offsets(sizes) + np.uint64(head)
+    n = int(off[-1]) + tail
+    keys = rng.integers(0, 1 << 32, n, dtype=np.uint32)
+    keys[head: head + 40] = keys[head]  # ties
+    dk, doff = to_dev(keys), to_dev(off)
+    ko = torch.full((n,), -7, dtype=torch.int32, device="cuda")
+    io = torch.full((n,), -9, dtype=index_dtype, device="cuda")
+    rs.rs_sort_segmented(dk, doff, None, ko, io, argsort=True, index_dtype=index_dtype, ctx=ctx)
+    ctx.check()
+    got_k, got_i = from_dev(ko, np.uint32), io.cpu().numpy().astype(np.int64)
+    for s in range(len(sizes)):
+        lo, hi = int(off[s]), int(off[s + 1])
+        ref_k, perm, _ = oracle.sort_u32(keys[lo:hi])
+        assert np.array_equal(got_k[lo:hi], ref_k)
+        assert np.array_equal(got_i[lo:hi], perm.astype(np.int64))
+    assert (got_i[:head] == -9).all() and (got_i[n - tail:] == -9).all()
+    assert (got_k[:head] == np.uint32(0xFFFFFFF9)).all()
+    assert (got_k[n - tail:] == np.uint32(0xFFFFFFF9)).all()
