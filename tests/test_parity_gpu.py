@@ -168,7 +168,8 @@ NARROW_TILE = 16 * 256
 
 @pytest.mark.parametrize("n", [4097, 2 * NARROW_TILE - 1, 2 * NARROW_TILE, 2 * NARROW_TILE + 1,
                                5 * NARROW_TILE + 17, 1 << 19, (1 << 19) + 3])
-@pytest.mark.parametrize("kind", ["u32_keys", "u32_pairs", "f32_pairs", "dec_keys", "dec_pairs"])
+@pytest.mark.parametrize("kind", ["u32_keys", "u32_pairs", "f32_keys", "f32_pairs", "dec_keys",
+                                  "dec_pairs"])
 def test_narrow_tile_boundaries(rs, ctx, oracle, narrow_tiles, kind, n):
     """The narrow pass tile (16 keys per thread) at its tile boundaries, for
     every shape that has one, against the oracle."""
@@ -178,7 +179,7 @@ def test_narrow_tile_boundaries(rs, ctx, oracle, narrow_tiles, kind, n):
         keys[1::5] = keys[0::5][: keys[1::5].size]  # ties
         ref_k, perm, _ = oracle.sort_u32(keys)
         kdt = np.uint32
-    elif kind == "f32_pairs":
+    elif kind.startswith("f32"):
         keys = np.round(rng.standard_normal(n) * 100).astype(np.float32)
         _, perm, _ = oracle.sort_float(keys)
         ref_k = keys[perm.astype(np.int64)]
@@ -191,10 +192,12 @@ def test_narrow_tile_boundaries(rs, ctx, oracle, narrow_tiles, kind, n):
     if kind.endswith("keys"):
         if kind == "u32_keys":
             out = rs.rs_sort_u32(to_dev(keys), ctx=ctx)
+        elif kind == "f32_keys":
+            out, _ = rs.rs_sort_pairs(to_dev(keys), None, ctx=ctx)
         else:
             out = rs.rs_sort_fixed_decimal(to_dev(keys), 6, 3, ctx=ctx)
         ctx.check()
-        assert np.array_equal(from_dev(out, kdt), ref_k)
+        assert np.array_equal(from_dev(out, kdt).view(np.uint8), ref_k.view(np.uint8))
     else:
         vals = np.arange(n, dtype=np.uint32)
         ko, vo = rs.rs_sort_pairs(to_dev(keys), to_dev(vals),
