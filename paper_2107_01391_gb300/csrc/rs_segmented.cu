@@ -11,10 +11,11 @@
 //          after them is as small), a CTA takes eight at a time and each
 //          warp sorts one: two keys per lane, each ranked by counting the
 //          keys before it in (cell, position) order;
-//        - a segment of at most 4096 keys (one tile) is loaded once into
-//          registers and sorted entirely on chip: one rank-and-scatter
-//          through shared memory per 8-bit digit group, then one coalesced
-//          write (16 bytes per u32 key+value pair in total);
+//        - a segment of at most 4096 keys (one tile; 4095 where step 7
+//          runs) is loaded once into registers, spread over every warp, and
+//          sorted entirely on chip: one rank-and-scatter through shared
+//          memory per 8-bit digit group, then one coalesced write (16 bytes
+//          per u32 key+value pair in total);
 //        - a longer segment below 2^DEV_MIN_LOG2 keys is first read once
 //          to count all its digit groups, then sorted by its CTA alone: per
 //          non-trivial group a sweep over its tiles in input order with
@@ -35,6 +36,9 @@
 //                        each ranked like the device-wide pass and placed
 //                        with a decoupled look-back that stops at its
 //                        segment's first tile.
+//   7. seg_rows_kernel   (4-byte cells with no value, a 4-byte value or an
+//                        argsort) the segments of 4096 .. 8191 keys, each
+//                        sorted whole on chip by one CTA; step 3 skips them.
 
 #include <cuda_runtime.h>
 
@@ -62,6 +66,15 @@ constexpr uint64_t SEG_MAX_LEN = RS_MAX_N;  // look-back words of the device tie
 constexpr uint32_t DEV_MIN_LOG2 = 13;
 constexpr uint32_t DEV_CLASS_MAX = 63 - DEV_MIN_LOG2;
 static_assert((1u << DEV_MIN_LOG2) > SEG_TILE, "the device tier starts above the on-chip tier");
+
+// Size classes (leading zeros of the 64-bit length) that bound the tiers in
+// the ordered list: the row tier is the class of 2^12 .. 2^13-1 keys, and the
+// warp tier starts at the class of 32 .. 63 keys.
+constexpr uint32_t ROW_CLASS = 63 - 12;
+constexpr uint32_t WARP_CLASS = 63 - 5;
+static_assert(SEG_TILE == (1u << 12) && ROW_TILE == (1u << 13) && DEV_MIN_LOG2 == 13,
+              "the row tier is one size class between the on-chip and device tiers");
+static_assert(WARP_SEG_MAX == 63, "the warp tier is the classes of 1 .. 63 keys");
 
 struct SegControl {
     uint32_t class_count[SIZE_CLASSES];
@@ -118,7 +131,7 @@ struct SegArgs {
     // device-tier segments of at least this many keys are counted tile by
     // tile by seg_count_kernel; shorter ones by the CTA that takes them
     uint64_t count_par_min;
-    // segments of SEG_TILE+1 .. ROW_TILE-1 keys are sorted whole on chip by
+    // segments of SEG_TILE .. ROW_TILE-1 keys are sorted whole on chip by
     // seg_rows_kernel (4-byte cells with no value, a 4-byte value or an
     // argsort); seg_sort_kernel leaves them out
     uint32_t row_tier;
@@ -326,21 +339,23 @@ __global__ void __launch_bounds__(BLOCK) seg_order_kernel(SegArgs a, uint32_t* o
     }
 }
 
-// Load one tile (positions [base, base+valid) of `src`) warp-striped.  With
-// iota_from != ~0 the values are generated: position - iota_from.
+// Load one tile (positions [base, base+valid) of `src`) warp-striped over
+// `rows` item rows per warp (rank_scatter's layout).  With iota_from != ~0
+// the values are generated: position - iota_from.
 template <class C, typename VS, bool kPairs, bool kDecode>
 __device__ __forceinline__ void load_tile(const void* ksrc, const VS* vsrc, uint64_t base,
                                           uint32_t valid, const CodecParams& prm,
                                           uint64_t iota_from, typename C::Cell (&k)[SEG_IPT],
-                                          VS (&v)[SEG_IPT], uint32_t* status) {
+                                          VS (&v)[SEG_IPT], uint32_t* status,
+                                          uint32_t rows = SEG_IPT) {
     using Cell = typename C::Cell;
     const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
-    const uint32_t w0 = warp * 32 * SEG_IPT + lane;
+    const uint32_t w0 = warp * 32 * rows + lane;
     bool ok = true;
 #pragma unroll
     for (int i = 0; i < SEG_IPT; i++) {
         const uint32_t j = w0 + i * 32;
-        if (j < valid) {
+        if ((uint32_t)i < rows && j < valid) {
             if constexpr (kDecode)
                 k[i] = C::decode(static_cast<const typename C::In*>(ksrc)[base + j], prm, ok);
             else
@@ -428,20 +443,21 @@ __global__ void __launch_bounds__(BLOCK, seg_ctas_per_sm<C, V>()) seg_sort_kerne
     extern __shared__ __align__(16) unsigned char smem_dyn[];
     const Stage<Cell, VS, kPairs, SEG_TILE> stage{smem_dyn};
     const uint32_t t = threadIdx.x, lane = lane_id(), warp = t >> 5;
+    // The list is ordered by size class, largest first.  One counter step
+    // claims one entry before the warp tier, skipping the row tier's (sorted
+    // by seg_rows_kernel), or WARPS entries of the warp tier, one per warp.
+    const uint64_t warp_from = __ldcg(&a.ctl->class_cursor[WARP_CLASS - 1]);
+    const uint64_t row_end = a.row_tier ? __ldcg(&a.ctl->class_cursor[ROW_CLASS]) : 0;
+    const uint64_t row_skip = a.row_tier ? __ldcg(&a.ctl->class_count[ROW_CLASS]) : 0;
+    const uint64_t row_begin = row_end - row_skip;
 
     while (true) {
         if (t == 0) {
-            // The list is ordered by size class, largest first: once the next
-            // entry is a warp-sized segment every later one is too, so take
-            // one per warp.
-            uint32_t take = 1;
-            const uint32_t peek = ld_relaxed(&a.ctl->work);
-            uint64_t plo, phi;
-            if (peek < a.num_segs && seg_bounds(a, a.order[peek], plo, phi) &&
-                phi - plo <= WARP_SEG_MAX)
-                take = WARPS;
-            s_first = atomicAdd(&a.ctl->work, take);
-            s_take = take;
+            const uint64_t u = atomicAdd(&a.ctl->work, 1u);
+            const uint64_t e = u < row_begin ? u : u + row_skip;  // order entry
+            const uint64_t first = e < warp_from ? e : warp_from + (e - warp_from) * WARPS;
+            s_first = (uint32_t)min(first, (uint64_t)a.num_segs);
+            s_take = e < warp_from ? 1u : (uint32_t)WARPS;
         }
         __syncthreads();
         const uint32_t first_w = s_first, take = s_take;
@@ -462,27 +478,29 @@ __global__ void __launch_bounds__(BLOCK, seg_ctas_per_sm<C, V>()) seg_sort_kerne
         Cell k[SEG_IPT];
         VS v[SEG_IPT];
         const bool device_tier = first_w < __ldcg(&a.ctl->n_large);
-        if (a.row_tier && !device_tier && len > SEG_TILE && len < ROW_TILE) continue;
+        if (a.row_tier && !device_tier && len >= SEG_TILE && len < ROW_TILE) continue;
         if (!device_tier && len <= SEG_TILE) {
-            // ---- one tile: sorted on chip, read once and written once ----
+            // ---- one tile: sorted on chip, read once and written once, spread
+            // over every warp in ceil(len / BLOCK) item rows ----
             const uint32_t valid = (uint32_t)len;
+            const uint32_t rows = (valid + BLOCK - 1) / BLOCK;
             load_tile<C, VS, kPairs, true>(a.keys_in, vin, lo, valid, a.prm,
-                                           a.iota ? lo : ~0ull, k, v, a.status);
+                                           a.iota ? lo : ~0ull, k, v, a.status, rows);
+            const uint32_t w0 = warp * 32 * rows + lane;
             for (uint32_t p = 0; p < a.passes; p++) {
-                rank_scatter<Cell, VS, SEG_IPT, kPairs>(k, v, valid, p * RADIX_BITS, ts, stage);
-                const uint32_t w0 = warp * 32 * SEG_IPT + lane;
+                rank_scatter<Cell, VS, SEG_IPT, kPairs>(k, v, valid, p * RADIX_BITS, ts, stage,
+                                                        nullptr, rows);
 #pragma unroll
                 for (int i = 0; i < SEG_IPT; i++) {
                     const uint32_t j = w0 + i * 32;
-                    if (j < valid) stage.get(j, k[i], v[i]);
+                    if ((uint32_t)i < rows && j < valid) stage.get(j, k[i], v[i]);
                 }
                 __syncthreads();  // the staged tile is rewritten by the next group
             }
-            const uint32_t w0 = warp * 32 * SEG_IPT + lane;
 #pragma unroll
             for (int i = 0; i < SEG_IPT; i++) {
                 const uint32_t j = w0 + i * 32;
-                if (j < valid) {
+                if ((uint32_t)i < rows && j < valid) {
                     static_cast<Out*>(a.keys_out)[lo + j] = C::encode(k[i], a.prm);
                     if constexpr (kPairs) vout[lo + j] = v[i];
                 }
@@ -599,17 +617,19 @@ __global__ void __launch_bounds__(BLOCK, seg_ctas_per_sm<C, V>()) seg_sort_kerne
             __syncthreads();
             for (uint64_t base = 0; base < len; base += SEG_TILE) {
                 const uint32_t valid = (uint32_t)min((uint64_t)SEG_TILE, len - base);
+                const uint32_t rows = (valid + BLOCK - 1) / BLOCK;  // the last tile: spread
                 if (first)
                     load_tile<C, VS, kPairs, true>(ksrc, vsrc, base, valid, a.prm,
-                                                   a.iota ? 0ull : ~0ull, k, v, a.status);
+                                                   a.iota ? 0ull : ~0ull, k, v, a.status, rows);
                 else
                     load_tile<C, VS, kPairs, false>(ksrc, vsrc, base, valid, a.prm, ~0ull, k, v,
-                                                    a.status);
+                                                    a.status, rows);
                 if (valid == SEG_TILE)  // every tile but a segment's last: no position tests
                     rank_scatter<Cell, VS, SEG_IPT, kPairs, false, true>(k, v, valid, shift, ts,
                                                                          stage, s_run);
                 else
-                    rank_scatter<Cell, VS, SEG_IPT, kPairs>(k, v, valid, shift, ts, stage, s_run);
+                    rank_scatter<Cell, VS, SEG_IPT, kPairs>(k, v, valid, shift, ts, stage, s_run,
+                                                            rows);
                 for (uint32_t j = t; j < valid; j += BLOCK) {
                     Cell c;
                     VS val;
@@ -635,16 +655,13 @@ __global__ void __launch_bounds__(BLOCK, seg_ctas_per_sm<C, V>()) seg_sort_kerne
     }
 }
 
-// The row tier: segments of SEG_TILE+1 .. ROW_TILE-1 keys, which are exactly
-// the size class of lengths 2^12 .. 2^13-1 of the ordered list (less those of
-// 2^12 keys, which seg_sort_kernel keeps on chip), each sorted whole on chip
-// by one CTA as the row kernel sorts an equal row: 32 keys per thread, one
-// read, a rank per non-trivial digit group, one write (16 bytes per key and
-// value instead of the sweep's 4 + 16 per digit group).  A row shorter than
-// the tile is padded and ranked as a whole tile, with no position tests.
-constexpr uint32_t ROW_CLASS = 63 - 12;  // leading zeros of 2^12 .. 2^13-1
-static_assert(SEG_TILE == (1u << 12) && ROW_TILE == (1u << 13) && DEV_MIN_LOG2 == 13,
-              "the row tier is one size class between the on-chip and device tiers");
+// The row tier: segments of SEG_TILE .. ROW_TILE-1 keys, which are exactly
+// the size class of lengths 2^12 .. 2^13-1 of the ordered list, each sorted
+// whole on chip by one CTA as the row kernel sorts an equal row: 32 keys per
+// thread, one read, a rank per non-trivial digit group, one write (16 bytes
+// per key and value instead of the sweep's 4 + 16 per digit group).  A row
+// shorter than the tile is padded to a multiple of 4 * BLOCK keys and ranked
+// spread over every warp, with no position tests.
 
 template <class C, typename V, typename VR>
 __global__ void __launch_bounds__(BLOCK, 2) seg_rows_kernel(SegArgs a) {
@@ -670,8 +687,43 @@ __global__ void __launch_bounds__(BLOCK, 2) seg_rows_kernel(SegArgs a) {
         uint64_t lo, hi;
         if (!seg_bounds(a, a.order[r], lo, hi)) continue;  // (uniform per CTA)
         const uint64_t len = hi - lo;
-        if (len <= SEG_TILE || len >= ROW_TILE) continue;
+        if (len < SEG_TILE || len >= ROW_TILE) continue;
         sort_row<C, V, ROW_IPT, VR, true, false>(ra, lo, (uint32_t)len, ts, s_ref, stage);
+    }
+}
+
+// The device tier's count and rank over the first `rows` item rows of a
+// warp (all of them with kAll: a full tile, no row test).  rows is a
+// multiple of ROWS_Q.
+template <bool kAll, int IPT, typename Cell>
+__device__ __forceinline__ void count_rows(const Cell (&k)[IPT], uint32_t* wh, uint32_t shift,
+                                           uint32_t rows) {
+#pragma unroll
+    for (int i = 0; i < IPT; i++) {
+        if (!kAll && i % ROWS_Q == 0 && (uint32_t)i >= rows) break;  // block-uniform
+        atomicAdd(&wh[digit_of(k[i], shift)], 1u);
+    }
+}
+
+// Stable rank in (cell, input) order: wh holds the warp's next position of
+// each cell; every item is written to its position in `stage`.
+template <bool kAll, bool kLut, int IPT, typename Cell, typename VS, bool kPairs, int TILE>
+__device__ __forceinline__ void rank_rows(const Cell (&k)[IPT], const VS (&v)[IPT], uint32_t* wh,
+                                          uint32_t shift, uint32_t rows, const LaneBits& lbits,
+                                          const Stage<Cell, VS, kPairs, TILE>& stage) {
+    const uint32_t lt_mask = lanemask_lt(), gt_mask = lanemask_gt();
+#pragma unroll
+    for (int i = 0; i < IPT; i++) {
+        if (!kAll && i % ROWS_Q == 0 && (uint32_t)i >= rows) break;  // block-uniform
+        const uint32_t dk = digit_of(k[i], shift);
+        const uint32_t peers = peer_mask<kLut>(dk, lbits);
+        uint32_t* slot_p = &wh[dk];
+        const uint32_t pos0 = *slot_p;
+        const uint32_t below = __popc(peers & lt_mask);
+        __syncwarp();
+        if ((peers & gt_mask) == 0) *slot_p = pos0 + below + 1;
+        stage.put(pos0 + below, k[i], v[i]);
+        __syncwarp();
     }
 }
 
@@ -705,7 +757,6 @@ __global__ void __launch_bounds__(BLOCK, 2) seg_pass_kernel(SegArgs a, uint32_t 
     const LaneBits lbits = lane_bits();
 
     const uint32_t t = threadIdx.x, lane = lane_id(), warp = t >> 5;
-    const uint32_t lt_mask = lanemask_lt(), gt_mask = lanemask_gt();
     const uint32_t n_large = __ldcg(&a.ctl->n_large);
     const uint32_t dev_tiles = (uint32_t)min((uint64_t)__ldcg(&a.ctl->dev_tiles), a.max_tiles);
     uint32_t* const lookback = a.lookback[pass & 1];
@@ -768,6 +819,13 @@ __global__ void __launch_bounds__(BLOCK, 2) seg_pass_kernel(SegArgs a, uint32_t 
         }
         const bool full = tbase + TILE <= len;
         const uint32_t valid = full ? TILE : (uint32_t)(len - tbase);
+        // a segment's last tile is spread over every warp in `rows` item rows
+        // (a multiple of ROWS_Q), so its count and rank cost what it holds,
+        // not a whole tile
+        static_assert(IPT % ROWS_Q == 0, "item rows are skipped ROWS_Q at a time");
+        const uint32_t rows =
+            full ? (uint32_t)IPT
+                 : min((uint32_t)IPT, (valid + BLOCK * ROWS_Q - 1) / (BLOCK * ROWS_Q) * ROWS_Q);
         const uint32_t from_end = __popc(use) - 1 - __popc(use & ((1u << pass) - 1u));
         const bool first = (use & ((1u << pass) - 1u)) == 0, last = from_end == 0;
         const uint32_t dstb = (from_end & 1u) ? BUF_TMP : BUF_OUT;
@@ -779,8 +837,8 @@ __global__ void __launch_bounds__(BLOCK, 2) seg_pass_kernel(SegArgs a, uint32_t 
         Cell* const out_cells =
             reinterpret_cast<Cell*>(static_cast<unsigned char*>(a.keys_out) + lo * sizeof(Out));
 
-        // ---- load (warp-striped: warp w owns tile items [w*32*IPT, (w+1)*32*IPT)) ----
-        const uint32_t w0 = warp * 32 * IPT + lane;
+        // ---- load (warp-striped: warp w owns tile items [w*32*rows, (w+1)*32*rows)) ----
+        const uint32_t w0 = warp * 32 * rows + lane;
         Cell k[IPT];
         VS v[IPT];
         if (srcb == BUF_IN) {
@@ -792,8 +850,9 @@ __global__ void __launch_bounds__(BLOCK, 2) seg_pass_kernel(SegArgs a, uint32_t 
             } else {
 #pragma unroll
                 for (int i = 0; i < IPT; i++)
-                    k[i] = w0 + i * 32 < valid ? C::decode(__ldcs(&in[i * 32]), a.prm, okd)
-                                               : ~Cell(0);
+                    k[i] = (uint32_t)i < rows && w0 + i * 32 < valid
+                               ? C::decode(__ldcs(&in[i * 32]), a.prm, okd)
+                               : ~Cell(0);
             }
         } else {
             const Cell* in = (srcb == BUF_TMP ? tmp_cells : out_cells) + tbase + w0;
@@ -802,7 +861,8 @@ __global__ void __launch_bounds__(BLOCK, 2) seg_pass_kernel(SegArgs a, uint32_t 
                 for (int i = 0; i < IPT; i++) k[i] = __ldcs(&in[i * 32]);
             } else {
 #pragma unroll
-                for (int i = 0; i < IPT; i++) k[i] = w0 + i * 32 < valid ? __ldcs(&in[i * 32]) : ~Cell(0);
+                for (int i = 0; i < IPT; i++)
+                    k[i] = (uint32_t)i < rows && w0 + i * 32 < valid ? __ldcs(&in[i * 32]) : ~Cell(0);
             }
         }
         if constexpr (kPairs) {
@@ -818,14 +878,17 @@ __global__ void __launch_bounds__(BLOCK, 2) seg_pass_kernel(SegArgs a, uint32_t 
                     for (int i = 0; i < IPT; i++) v[i] = __ldcs(&vin[i * 32]);
                 } else {
 #pragma unroll
-                    for (int i = 0; i < IPT; i++) v[i] = w0 + i * 32 < valid ? __ldcs(&vin[i * 32]) : VS(0);
+                    for (int i = 0; i < IPT; i++)
+                        v[i] = (uint32_t)i < rows && w0 + i * 32 < valid ? __ldcs(&vin[i * 32]) : VS(0);
                 }
             }
         }
 
         // ---- counts per (warp, cell), the tile's aggregate, tile-local starts ----
-#pragma unroll
-        for (int i = 0; i < IPT; i++) atomicAdd(&ws[warp][digit_of(k[i], shift)], 1u);
+        if (full)
+            count_rows<true>(k, ws[warp], shift, rows);
+        else
+            count_rows<false>(k, ws[warp], shift, rows);
         __syncthreads();
         const uint32_t d = t;  // this thread's cell
         uint32_t run = 0;
@@ -836,7 +899,7 @@ __global__ void __launch_bounds__(BLOCK, 2) seg_pass_kernel(SegArgs a, uint32_t 
             run += x;
         }
         // padding items carry cell ~0 (digit 255) and sit after every real item
-        const uint32_t count = d == RADIX - 1 ? run - (TILE - valid) : run;
+        const uint32_t count = d == RADIX - 1 ? run - (BLOCK * rows - valid) : run;
         uint32_t* lb = lookback + (uint64_t)g * RADIX;
         st_relaxed(&lb[d], (lt == 0 ? LB_INCLUSIVE : LB_AGGREGATE) | count);
         uint32_t tile_total;
@@ -846,19 +909,10 @@ __global__ void __launch_bounds__(BLOCK, 2) seg_pass_kernel(SegArgs a, uint32_t 
         __syncthreads();
 
         // ---- stable rank in (cell, input) order, scattered into shared memory ----
-#pragma unroll
-        for (int i = 0; i < IPT; i++) {
-            const uint32_t dk = digit_of(k[i], shift);
-            const uint32_t peers = peer_mask<kLut>(dk, lbits);
-            uint32_t* slot_p = &ws[warp][dk];
-            const uint32_t pos0 = *slot_p;
-            const uint32_t below = __popc(peers & lt_mask);
-            __syncwarp();
-            if ((peers & gt_mask) == 0) *slot_p = pos0 + below + 1;
-            const uint32_t pos = pos0 + below;
-            stage.put(pos, k[i], v[i]);
-            __syncwarp();
-        }
+        if (full)
+            rank_rows<true, kLut>(k, v, ws[warp], shift, rows, lbits, stage);
+        else
+            rank_rows<false, kLut>(k, v, ws[warp], shift, rows, lbits, stage);
 
         // ---- look-back over the segment's earlier tiles ----
         uint32_t before = 0;
@@ -1001,13 +1055,22 @@ rs_status run_segmented(rs_ctx* ctx, const void* keys_in, void* keys_out, const 
         };
         const size_t vb = kPairs ? sizeof(VS) : 0;
         rs_status rs_;
-        if (len <= SMALL_TILE) {
+        if (len == SMALL_TILE) {
             rs_ = launch(tile_rows_kernel<C, V, SMALL_IPT>, SMALL_TILE, vb);
+        } else if (len < SMALL_TILE) {
+            rs_ = launch(tile_rows_kernel<C, V, SMALL_IPT, V, true>, SMALL_TILE, vb);
         } else {
-            if constexpr (!kPairs || sizeof(VS) == 4)
-                rs_ = launch(tile_rows_kernel<C, V, ROW_IPT>, ROW_TILE, vb);
-            else  // an argsort with 8-byte indices: carried as 32-bit words
-                rs_ = launch(tile_rows_kernel<C, V, ROW_IPT, uint32_t>, ROW_TILE, 4);
+            if constexpr (!kPairs || sizeof(VS) == 4) {
+                if (len == ROW_TILE)
+                    rs_ = launch(tile_rows_kernel<C, V, ROW_IPT>, ROW_TILE, vb);
+                else
+                    rs_ = launch(tile_rows_kernel<C, V, ROW_IPT, V, true>, ROW_TILE, vb);
+            } else {  // an argsort with 8-byte indices: carried as 32-bit words
+                if (len == ROW_TILE)
+                    rs_ = launch(tile_rows_kernel<C, V, ROW_IPT, uint32_t>, ROW_TILE, 4);
+                else
+                    rs_ = launch(tile_rows_kernel<C, V, ROW_IPT, uint32_t, true>, ROW_TILE, 4);
+            }
         }
         if (rs_ != RS_OK) return rs_;
         return cudaGetLastError() == cudaSuccess ? RS_OK : RS_ERR_CUDA;

@@ -123,14 +123,18 @@ rs_status run_sort_tile(rs_ctx* ctx, const void* keys_in, void* keys_out, const 
     if (n <= SMALL_TILE) {
         // one tile: one CTA sorts it on chip in a single launch (the
         // workspace is not touched)
-        auto kern = tile_rows_kernel<C, V, SMALL_IPT>;
+        // (a full tile and a shorter input are separate kernels)
+        const bool full = n == SMALL_TILE;
+        auto kern = full ? tile_rows_kernel<C, V, SMALL_IPT>
+                         : tile_rows_kernel<C, V, SMALL_IPT, V, true>;
         const size_t smem = SMALL_TILE * (sizeof(Cell) + (kPairs ? sizeof(V) : 0));
-        static std::atomic<bool> small_set[64];  // zero-initialised: false
-        if (ctx->device < 64 && !small_set[ctx->device].load(std::memory_order_acquire)) {
+        static std::atomic<bool> small_set[2][64];  // zero-initialised: false
+        std::atomic<bool>* set = ctx->device < 64 ? &small_set[full][ctx->device] : nullptr;
+        if (!set || !set->load(std::memory_order_acquire)) {
             if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem) != cudaSuccess)
                 return RS_ERR_CUDA;
-            small_set[ctx->device].store(true, std::memory_order_release);
+            if (set) set->store(true, std::memory_order_release);
         }
         RowsArgs ra{};
         ra.keys_in = keys_in;

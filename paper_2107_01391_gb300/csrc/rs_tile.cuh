@@ -21,6 +21,11 @@ struct TileShared {
 };
 
 // Positions [0, n_valid) of the tile hold keys; the rest are ignored.
+// `rows` (1 .. IPT): item rows per warp, so warp w holds positions
+// [w*32*rows, (w+1)*32*rows) in items 0 .. rows-1; a tile shorter than
+// BLOCK * IPT is spread over every warp with rows = ceil(n / BLOCK) instead of
+// filling the first warps, so its rank costs rows, not IPT, rounds per warp.
+// With kFull, rows is a multiple of ROWS_Q (or IPT).
 // Returns with `stage` holding the tile in (cell, input) order and
 // ts.count / ts.excl filled.  Every thread of the CTA must call it.
 // s_run (optional): running per-cell output offsets of a sweep over several
@@ -29,24 +34,28 @@ struct TileShared {
 // no barrier between tiles.
 // kLut: the table match (match_digit_lut) in place of match_digit, for
 // shapes whose register budget holds its five lane constants.  kFull: every
-// position of the tile holds a key (n_valid == BLOCK * IPT), so no position
-// is tested.
+// item of the first `rows` holds a key (n_valid == BLOCK * rows), so no
+// position is tested.
+constexpr uint32_t ROWS_Q = 4;  // granularity of a padded tile's item rows
+
 template <typename Cell, typename VS, int IPT, bool kPairs, bool kLut = false,
           bool kFull = false, int STILE>
 __device__ __forceinline__ void rank_scatter(const Cell (&k)[IPT], const VS (&v)[IPT],
                                              uint32_t n_valid, uint32_t shift, TileShared& ts,
                                              const Stage<Cell, VS, kPairs, STILE>& stage,
-                                             uint32_t* s_run = nullptr) {
+                                             uint32_t* s_run = nullptr, uint32_t rows = IPT) {
     const uint32_t t = threadIdx.x, lane = lane_id(), warp = t >> 5;
-    const uint32_t wbase = warp * 32 * IPT;
+    const uint32_t wbase = warp * 32 * rows;
     for (uint32_t d = lane; d < RADIX; d += 32) ts.wh[warp][d] = 0;
     __syncwarp();
     const uint32_t warp_items =
-        kFull ? 32u * IPT : (wbase < n_valid ? min(n_valid - wbase, 32u * IPT) : 0u);
+        kFull ? 32u * rows : (wbase < n_valid ? min(n_valid - wbase, 32u * rows) : 0u);
 #pragma unroll
-    for (int i = 0; i < IPT; i++)
+    for (int i = 0; i < IPT; i++) {
+        if (kFull && i % ROWS_Q == 0 && (uint32_t)i >= rows) break;  // block-uniform
         if (kFull || (uint32_t)i * 32 + lane < warp_items)
             atomicAdd(&ts.wh[warp][digit_of(k[i], shift)], 1u);
+    }
     __syncthreads();
 
     uint32_t run = 0;
@@ -69,7 +78,9 @@ __device__ __forceinline__ void rank_scatter(const Cell (&k)[IPT], const VS (&v)
     const LaneBits lbits = lane_bits();
 #pragma unroll
     for (int i = 0; i < IPT; i++) {
-        if (!kFull && (uint32_t)i * 32 >= warp_items) break;  // warp-uniform
+        if (kFull ? i % ROWS_Q == 0 && (uint32_t)i >= rows
+                  : (uint32_t)i * 32 >= warp_items)
+            break;  // warp-uniform
         const bool valid = kFull || (uint32_t)i * 32 + lane < warp_items;
         const uint32_t vmask = kFull ? 0xffffffffu : __ballot_sync(0xffffffffu, valid);
         const uint32_t d = digit_of(k[i], shift);
@@ -120,11 +131,13 @@ struct RowsArgs {
 
 // One row of n keys starting at key `base`: load, one rank per non-trivial
 // digit group, write.  kCheckIO: loads and stores test the position (n may
-// be below BLOCK * IPT).  kCheckRank: the ranks test it too; without it a
-// short row is ranked as a whole tile whose positions from n on hold padding
-// keys of the largest cell, which start after every real key and so stay in
-// the tile's last positions through every stable group (the trivial-group
-// test looks at the real keys only).
+// be below BLOCK * IPT), and the row is spread over every warp in `rows`
+// item rows, ceil(n / BLOCK) rounded up to a multiple of ROWS_Q.
+// kCheckRank: the ranks test it too; without it a short row is ranked as
+// BLOCK * rows keys whose positions from n on hold padding keys of the
+// largest cell, which start after every real key and so stay in the last
+// positions through every stable group (the trivial-group test looks at the
+// real keys only).
 template <class C, typename V, int IPT, typename VR, bool kCheckIO, bool kCheckRank>
 __device__ __forceinline__ uint32_t sort_row(const RowsArgs& a, uint64_t base, uint32_t n,
                                              TileShared& ts,
@@ -143,9 +156,12 @@ __device__ __forceinline__ uint32_t sort_row(const RowsArgs& a, uint64_t base, u
     using VM = typename std::conditional<kPairs, V, uint32_t>::type;
     // the table match where the 32-key rows leave room for its constants
     constexpr bool kLut = IPT == ROW_IPT && sizeof(Cell) == 4 && sizeof(VS) == 4;
-    constexpr uint32_t TILE = BLOCK * IPT;
     const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
-    const uint32_t w0 = warp * 32 * IPT + lane;  // warp-striped: input order
+    static_assert(IPT % ROWS_Q == 0, "item rows are skipped ROWS_Q at a time");
+    const uint32_t rows =
+        kCheckIO ? min((uint32_t)IPT, (n + BLOCK * ROWS_Q - 1) / (BLOCK * ROWS_Q) * ROWS_Q)
+                 : (uint32_t)IPT;
+    const uint32_t w0 = warp * 32 * rows + lane;  // warp-striped: input order
     Cell k[IPT];
     VS v[IPT];
     bool ok = true;
@@ -154,6 +170,7 @@ __device__ __forceinline__ uint32_t sort_row(const RowsArgs& a, uint64_t base, u
         const uint32_t j = w0 + i * 32;
         k[i] = ~Cell(0);
         v[i] = VS(0);
+        if (kCheckIO && i % ROWS_Q == 0 && (uint32_t)i >= rows) break;  // block-uniform
         if (!kCheckIO || j < n) {
             k[i] = C::decode(static_cast<const In*>(a.keys_in)[base + j], a.prm, ok);
             if constexpr (kPairs)
@@ -169,14 +186,17 @@ __device__ __forceinline__ uint32_t sort_row(const RowsArgs& a, uint64_t base, u
         const uint32_t shift = p * RADIX_BITS;
         bool same = true;
 #pragma unroll
-        for (int i = 0; i < IPT; i++)
+        for (int i = 0; i < IPT; i++) {
+            if (kCheckIO && i % ROWS_Q == 0 && (uint32_t)i >= rows) break;
             if (!kCheckIO || w0 + i * 32 < n) same &= digit_of(k[i], shift) == digit_of(ref, shift);
+        }
         if (__syncthreads_and(same)) continue;  // every key in one cell
         moved++;
-        rank_scatter<Cell, VS, IPT, kPairs, kLut, !kCheckRank>(k, v, kCheckRank ? n : TILE, shift,
-                                                              ts, stage);
+        rank_scatter<Cell, VS, IPT, kPairs, kLut, !kCheckRank>(
+            k, v, kCheckRank ? n : BLOCK * rows, shift, ts, stage, nullptr, rows);
 #pragma unroll
         for (int i = 0; i < IPT; i++) {
+            if (kCheckIO && i % ROWS_Q == 0 && (uint32_t)i >= rows) break;
             const uint32_t j = w0 + i * 32;
             if (!kCheckRank || j < n) stage.get(j, k[i], v[i]);
         }
@@ -184,6 +204,7 @@ __device__ __forceinline__ uint32_t sort_row(const RowsArgs& a, uint64_t base, u
     }
 #pragma unroll
     for (int i = 0; i < IPT; i++) {
+        if (kCheckIO && i % ROWS_Q == 0 && (uint32_t)i >= rows) break;
         const uint32_t j = w0 + i * 32;
         if (!kCheckIO || j < n) {
             static_cast<Out*>(a.keys_out)[base + j] = C::encode(k[i], a.prm);
@@ -198,7 +219,10 @@ __device__ __forceinline__ uint32_t sort_row(const RowsArgs& a, uint64_t base, u
 // BLOCK * IPT, so they travel as 32-bit words whatever their output width.
 // At the start of each row the CTA prefetches its next row (row + gridDim.x)
 // into L2 with one TMA bulk prefetch, so that row's loads do not wait on DRAM.
-template <class C, typename V, int IPT, typename VR = V>
+// kShort: rows shorter than the tile (padded, spread over every warp);
+// otherwise every row fills the tile.  The two are separate kernels so that
+// each is register-allocated for its own loop.
+template <class C, typename V, int IPT, typename VR = V, bool kShort = false>
 __global__ void __launch_bounds__(BLOCK, 2) tile_rows_kernel(RowsArgs a) {
     using Cell = typename C::Cell;
     using In = typename C::In;
@@ -212,7 +236,7 @@ __global__ void __launch_bounds__(BLOCK, 2) tile_rows_kernel(RowsArgs a) {
     __shared__ Cell s_ref;
     extern __shared__ __align__(16) unsigned char smem_dyn[];
     const Stage<Cell, VS, kPairs, TILE> stage{smem_dyn};
-    const uint32_t n = a.len;
+    const uint32_t n = kShort ? a.len : TILE;  // a full-row launch has a.len == TILE
     uint32_t moved = 0;
 
     for (uint64_t row = blockIdx.x; row < a.rows; row += gridDim.x) {
@@ -227,10 +251,10 @@ __global__ void __launch_bounds__(BLOCK, 2) tile_rows_kernel(RowsArgs a) {
                 if ((((uintptr_t)vp | vb) & 15) == 0) bulk_prefetch_l2(vp, vb);
             }
         }
-        if (n == TILE)
-            moved = sort_row<C, V, IPT, VR, false, false>(a, row * n, n, ts, s_ref, stage);
+        if constexpr (kShort)
+            moved = sort_row<C, V, IPT, VR, true, false>(a, row * n, n, ts, s_ref, stage);
         else
-            moved = sort_row<C, V, IPT, VR, true, true>(a, row * n, n, ts, s_ref, stage);
+            moved = sort_row<C, V, IPT, VR, false, false>(a, row * TILE, TILE, ts, s_ref, stage);
     }
     if (a.info && blockIdx.x == 0 && threadIdx.x == 0) {
         a.info->mode = MODE_PASSES;

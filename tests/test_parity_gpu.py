@@ -222,7 +222,7 @@ def test_default_tile_selection(rs, ctx, oracle):
         assert ctx.last_plan()["tiles"] == -(-n // tile)
 
 
-@pytest.mark.parametrize("n", [1, 2, 33, 1000, 4095, 4096])
+@pytest.mark.parametrize("n", [1, 2, 33, 257, 1000, 1025, 3073, 4095, 4096])
 @pytest.mark.parametrize("kind", ["u32_pairs", "u64_pairs", "u32_u64v_in_place", "dec_keys",
                                   "narrow_keys"])
 def test_single_tile_sorts(rs, ctx, oracle, kind, n):

@@ -351,3 +351,75 @@ def test_argsort_leaves_positions_outside_segments(rs, ctx, oracle, index_dtype,
     assert (got_i[:head] == -9).all() and (got_i[n - tail:] == -9).all()
     assert (got_k[:head] == np.uint32(0xFFFFFFF9)).all()
     assert (got_k[n - tail:] == np.uint32(0xFFFFFFF9)).all()
+
+
+# ---- partial tiles spread over every warp: lengths around multiples of the
+# block (256 keys) and of 4 item rows (1024 keys), in every tier, with keys
+# equal to the largest cell, which the padding of a short tile shares ----
+
+SPREAD_SIZES = [64, 65, 255, 257, 511, 767, 768, 769, 1023, 1025, 2049, 3071, 4095,  # on chip
+                4097, 4353, 5119, 5120, 5121, 6143, 7169, 8191,                       # row tier
+                8192, 9000, 10_239, 10_241, 10_240 + 255, 10_240 + 257, 10_240 + 1025,
+                2 * 10_240 + 3072, 2 * 10_240 + 3073, 3 * 10_240 - 1]                # device tier
+
+
+@pytest.mark.parametrize("spread", ["random", "ties_top"])
+def test_spread_partial_tiles(rs, ctx, oracle, spread):
+    rng = np.random.default_rng(11 if spread == "random" else 12)
+    off = _offsets(SPREAD_SIZES)
+    n = int(off[-1])
+    if spread == "random":
+        keys = rng.integers(0, 1 << 32, n, dtype=np.uint32)
+        keys[::97] = 0xFFFFFFFF
+    else:  # few values, the largest among them: trivial and moving groups mixed
+        keys = rng.choice(np.array([0, 1, 0xFFFFFF00, 0xFFFFFFFF], np.uint32), n)
+    vals = np.arange(n, dtype=np.uint32)
+    ref_k, perm = _oracle_segments(oracle, keys, off, oracle.sort_u32)
+    ko, vo = rs.rs_sort_segmented(to_dev(keys), to_dev(off), to_dev(vals), ctx=ctx)
+    ctx.check()
+    assert np.array_equal(from_dev(ko, np.uint32), ref_k)
+    base = np.repeat(off[:-1].astype(np.int64), np.diff(off).astype(np.int64))
+    assert np.array_equal(from_dev(vo, np.uint32).astype(np.int64), base + perm)
+    ko, idx = rs.rs_sort_segmented(to_dev(keys), to_dev(off), argsort=True, ctx=ctx)
+    ctx.check()
+    assert np.array_equal(from_dev(ko, np.uint32), ref_k)
+    assert np.array_equal(idx.cpu().numpy(), perm)
+
+
+@pytest.mark.parametrize("length", [100, 300, 1025, 4000, 4097, 5000, 8000])
+@pytest.mark.parametrize("kind", ["u32_pairs", "f32_argsort64", "u64_u64v"])
+def test_equal_short_rows_spread(rs, ctx, oracle, length, kind):
+    """Equal rows shorter than their tile: each row is ranked padded, spread
+    over every warp."""
+    rows = 7
+    rng = np.random.default_rng(length + len(kind))
+    n = rows * length
+    off = np.arange(0, n + 1, length, dtype=np.uint64)
+    base = np.repeat(off[:-1].astype(np.int64), length)
+    if kind == "u32_pairs":
+        keys = rng.integers(0, 1 << 32, n, dtype=np.uint32)
+        keys[::13] = 0xFFFFFFFF
+        vals = rng.integers(0, 1 << 32, n, dtype=np.uint32)
+        ko, vo = rs.rs_sort_segmented(to_dev(keys), None, to_dev(vals), num_segs=rows, ctx=ctx)
+        ctx.check()
+        ref_k, perm = _oracle_segments(oracle, keys, off, oracle.sort_u32)
+        assert np.array_equal(from_dev(ko, np.uint32), ref_k)
+        assert np.array_equal(from_dev(vo, np.uint32), vals[base + perm])
+    elif kind == "u64_u64v":
+        keys = W.u64_keys(n, seed_extra=length)
+        keys[::11] = np.uint64(0xFFFFFFFFFFFFFFFF)
+        vals = rng.integers(0, 1 << 63, n, dtype=np.uint64)
+        ko, vo = rs.rs_sort_segmented(to_dev(keys), None, to_dev(vals), num_segs=rows, ctx=ctx)
+        ctx.check()
+        ref_k, perm = _oracle_segments(oracle, keys, off, oracle.sort_u64)
+        assert np.array_equal(from_dev(ko, np.uint64), ref_k)
+        assert np.array_equal(from_dev(vo, np.uint64), vals[base + perm])
+    else:
+        x = rng.standard_normal(n).astype(np.float32)
+        x[::9] = np.float32(np.nan)  # NaN: the largest cell
+        ko, idx = rs.rs_sort_segmented(to_dev(x), None, num_segs=rows, argsort=True, ctx=ctx)
+        ctx.check()
+        ref, want = _oracle_float_rows(oracle, x.reshape(rows, length))
+        assert np.array_equal(idx.cpu().numpy().reshape(rows, length), ref)
+        assert np.array_equal(ko.cpu().numpy().reshape(rows, length).view(np.uint32),
+                              want.view(np.uint32))
