@@ -519,9 +519,18 @@ __global__ void __launch_bounds__(BLOCK, seg_ctas_per_sm<C, V>()) seg_sort_kerne
             __syncthreads();
             bool ok = true;
             const In* kin = static_cast<const In*>(a.keys_in);
-            // eight loads in flight per thread
+            // eight loads in flight per thread, and the segment streaming
+            // into L2 ahead of them: one bulk prefetch of the first PF_STEPS
+            // loop steps, then each step prefetches the one PF_STEPS on
             constexpr int U = 8;
-            for (uint64_t j = lo + t; j < hi; j += (uint64_t)U * BLOCK) {
+            constexpr uint64_t STEP = (uint64_t)U * BLOCK;
+            constexpr uint64_t PF_STEPS = 8;
+            if (t == 0) prefetch_lines_l2(kin + lo, min(len, PF_STEPS * STEP) * sizeof(In));
+            for (uint64_t j = lo + t; j < hi; j += STEP) {
+                if (t == 0 && j + PF_STEPS * STEP < hi) {  // j is the step's first key
+                    const uint64_t pf = j + PF_STEPS * STEP;
+                    prefetch_lines_l2(kin + pf, min(hi - pf, STEP) * sizeof(In));
+                }
                 In kv[U];
 #pragma unroll
                 for (int u = 0; u < U; u++) {
