@@ -11,12 +11,13 @@
 //          after them is as small), a CTA takes eight at a time and each
 //          warp sorts one: two keys per lane, each ranked by counting the
 //          keys before it in (cell, position) order;
-//        - a segment of at most 4096 keys (one tile; 4095 where step 7
-//          runs) is loaded once into registers, spread over every warp, and
+//        - (shapes without step 7) a segment of at most 4096 keys (one
+//          tile) is loaded once into registers, spread over every warp, and
 //          sorted entirely on chip: one rank-and-scatter through shared
 //          memory per 8-bit digit group, then one coalesced write (16 bytes
 //          per u32 key+value pair in total);
-//        - a longer segment below 2^DEV_MIN_LOG2 keys is first read once
+//        - (shapes without step 7) a longer segment below 2^DEV_MIN_LOG2
+//          keys is first read once
 //          to count all its digit groups, then sorted by its CTA alone: per
 //          non-trivial group a sweep over its tiles in input order with
 //          running cell offsets in shared memory (a CTA-sequential
@@ -37,8 +38,9 @@
 //                        with a decoupled look-back that stops at its
 //                        segment's first tile.
 //   7. seg_rows_kernel   (4-byte cells with no value, a 4-byte value or an
-//                        argsort) the segments of 4096 .. 8191 keys, each
-//                        sorted whole on chip by one CTA; step 3 skips them.
+//                        argsort) the segments of 64 .. 8191 keys, each
+//                        sorted whole on chip by one CTA in the row kernel's
+//                        8192-key tile; step 3 skips them.
 
 #include <cuda_runtime.h>
 
@@ -68,12 +70,18 @@ constexpr uint32_t DEV_CLASS_MAX = 63 - DEV_MIN_LOG2;
 static_assert((1u << DEV_MIN_LOG2) > SEG_TILE, "the device tier starts above the on-chip tier");
 
 // Size classes (leading zeros of the 64-bit length) that bound the tiers in
-// the ordered list: the row tier is the class of 2^12 .. 2^13-1 keys, and the
-// warp tier starts at the class of 32 .. 63 keys.
+// the ordered list: the row tier holds the classes of 2^ROW_MIN_LOG2 ..
+// 2^13-1 keys (ROW_CLASS, the largest, to ROW_LAST_CLASS), and the warp tier
+// starts at the class of 32 .. 63 keys.
+constexpr uint32_t ROW_MIN_LOG2 = 6;
+constexpr uint64_t ROW_MIN = 1ull << ROW_MIN_LOG2;
 constexpr uint32_t ROW_CLASS = 63 - 12;
+constexpr uint32_t ROW_LAST_CLASS = 63 - ROW_MIN_LOG2;
 constexpr uint32_t WARP_CLASS = 63 - 5;
-static_assert(SEG_TILE == (1u << 12) && ROW_TILE == (1u << 13) && DEV_MIN_LOG2 == 13,
-              "the row tier is one size class between the on-chip and device tiers");
+static_assert(ROW_TILE == (1u << 13) && DEV_MIN_LOG2 == 13,
+              "the row tier ends where the device tier starts");
+static_assert(ROW_MIN > WARP_SEG_MAX && ROW_MIN <= SEG_TILE,
+              "the row tier starts above the warp tier and at most one on-chip tile");
 static_assert(WARP_SEG_MAX == 63, "the warp tier is the classes of 1 .. 63 keys");
 
 struct SegControl {
@@ -131,7 +139,7 @@ struct SegArgs {
     // device-tier segments of at least this many keys are counted tile by
     // tile by seg_count_kernel; shorter ones by the CTA that takes them
     uint64_t count_par_min;
-    // segments of SEG_TILE .. ROW_TILE-1 keys are sorted whole on chip by
+    // segments of ROW_MIN .. ROW_TILE-1 keys are sorted whole on chip by
     // seg_rows_kernel (4-byte cells with no value, a 4-byte value or an
     // argsort); seg_sort_kernel leaves them out
     uint32_t row_tier;
@@ -447,9 +455,12 @@ __global__ void __launch_bounds__(BLOCK, seg_ctas_per_sm<C, V>()) seg_sort_kerne
     // claims one entry before the warp tier, skipping the row tier's (sorted
     // by seg_rows_kernel), or WARPS entries of the warp tier, one per warp.
     const uint64_t warp_from = __ldcg(&a.ctl->class_cursor[WARP_CLASS - 1]);
-    const uint64_t row_end = a.row_tier ? __ldcg(&a.ctl->class_cursor[ROW_CLASS]) : 0;
-    const uint64_t row_skip = a.row_tier ? __ldcg(&a.ctl->class_count[ROW_CLASS]) : 0;
-    const uint64_t row_begin = row_end - row_skip;
+    const uint64_t row_begin =
+        a.row_tier
+            ? __ldcg(&a.ctl->class_cursor[ROW_CLASS]) - __ldcg(&a.ctl->class_count[ROW_CLASS])
+            : 0;
+    const uint64_t row_skip =
+        a.row_tier ? __ldcg(&a.ctl->class_cursor[ROW_LAST_CLASS]) - row_begin : 0;
 
     while (true) {
         if (t == 0) {
@@ -478,7 +489,7 @@ __global__ void __launch_bounds__(BLOCK, seg_ctas_per_sm<C, V>()) seg_sort_kerne
         Cell k[SEG_IPT];
         VS v[SEG_IPT];
         const bool device_tier = first_w < __ldcg(&a.ctl->n_large);
-        if (a.row_tier && !device_tier && len >= SEG_TILE && len < ROW_TILE) continue;
+        if (a.row_tier && !device_tier && len >= ROW_MIN && len < ROW_TILE) continue;
         if (!device_tier && len <= SEG_TILE) {
             // ---- one tile: sorted on chip, read once and written once, spread
             // over every warp in ceil(len / BLOCK) item rows ----
@@ -664,13 +675,16 @@ __global__ void __launch_bounds__(BLOCK, seg_ctas_per_sm<C, V>()) seg_sort_kerne
     }
 }
 
-// The row tier: segments of SEG_TILE .. ROW_TILE-1 keys, which are exactly
-// the size class of lengths 2^12 .. 2^13-1 of the ordered list, each sorted
-// whole on chip by one CTA as the row kernel sorts an equal row: 32 keys per
-// thread, one read, a rank per non-trivial digit group, one write (16 bytes
-// per key and value instead of the sweep's 4 + 16 per digit group).  A row
-// shorter than the tile is padded to a multiple of 4 * BLOCK keys and ranked
-// spread over every warp, with no position tests.
+// The row tier: segments of ROW_MIN .. ROW_TILE-1 keys, which are exactly
+// the size classes ROW_CLASS .. ROW_LAST_CLASS of the ordered list, each
+// sorted whole on chip by one CTA as the row kernel sorts an equal row: one
+// read, a rank per non-trivial digit group, one write (16 bytes per key and
+// value; the sweep it replaced above 4096 keys moved 4 + 16 per digit
+// group).  A row shorter than the tile is padded to a multiple of 4 * BLOCK
+// keys and ranked spread over every warp, with no position tests, and the
+// table match (the row kernel's 32-key shape has room for its constants).
+// One CTA takes every gridDim.x-th entry: the list is ordered by size, so
+// each CTA gets the same mix.
 
 template <class C, typename V, typename VR>
 __global__ void __launch_bounds__(BLOCK, 2) seg_rows_kernel(SegArgs a) {
@@ -681,8 +695,9 @@ __global__ void __launch_bounds__(BLOCK, 2) seg_rows_kernel(SegArgs a) {
     __shared__ Cell s_ref;
     extern __shared__ __align__(16) unsigned char smem_dyn[];
     const Stage<Cell, VS, kPairs, ROW_TILE> stage{smem_dyn};
-    const uint32_t end = __ldcg(&a.ctl->class_cursor[ROW_CLASS]);
-    const uint32_t begin = end - __ldcg(&a.ctl->class_count[ROW_CLASS]);
+    const uint32_t begin =
+        __ldcg(&a.ctl->class_cursor[ROW_CLASS]) - __ldcg(&a.ctl->class_count[ROW_CLASS]);
+    const uint32_t end = __ldcg(&a.ctl->class_cursor[ROW_LAST_CLASS]);
     RowsArgs ra{};
     ra.keys_in = a.keys_in;
     ra.keys_out = a.keys_out;
@@ -696,7 +711,7 @@ __global__ void __launch_bounds__(BLOCK, 2) seg_rows_kernel(SegArgs a) {
         uint64_t lo, hi;
         if (!seg_bounds(a, a.order[r], lo, hi)) continue;  // (uniform per CTA)
         const uint64_t len = hi - lo;
-        if (len < SEG_TILE || len >= ROW_TILE) continue;
+        if (len < ROW_MIN || len >= ROW_TILE) continue;
         sort_row<C, V, ROW_IPT, VR, true, false>(ra, lo, (uint32_t)len, ts, s_ref, stage);
     }
 }
