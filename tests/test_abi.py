@@ -124,3 +124,30 @@ def test_context_needs_a_device(rs):
     assert rs.lib().rs_ctx_status(None, 0) == rs.RS_ERR_INVALID
     with pytest.raises(RuntimeError):
         rs.Context(0)
+
+
+def test_segmented_workspace_layout(rs):
+    """Host-side sizing of a segmented call: equal segments below the device
+    tier (2^13 keys) reserve no device-tier room, offsets always do; an
+    argsort to 8-byte indices carries 32-bit indices, so it needs the 4-byte
+    argsort's workspace plus n 32-bit words."""
+    fn = rs.lib().rs_sort_segmented
+    fake, z = ctypes.c_void_p(1), ctypes.c_void_p(256)
+
+    def ws(n, segs, offsets, vals_in, vb):
+        need = ctypes.c_size_t(0)
+        assert fn(fake, rs.RS_KEY_U32, z, z, z if vals_in else None, z, vb, n,
+                  z if offsets else None, segs, None, None, ctypes.byref(need), None) == rs.RS_OK
+        assert need.value % 256 == 0
+        return need.value
+
+    n = 1 << 24
+    short_equal = ws(n, n >> 12, False, True, 4)   # rows of 4096 keys
+    long_equal = ws(n, n >> 14, False, True, 4)    # rows of 16384 keys: device tier
+    with_offsets = ws(n, n >> 12, True, True, 4)
+    assert short_equal < with_offsets
+    assert long_equal == ws(n, n >> 14, True, True, 4)
+    assert short_equal >= 8 * n                     # cell and value ping-pong buffers
+    arg32 = ws(n, n >> 12, True, False, 4)
+    arg64 = ws(n, n >> 12, True, False, 8)
+    assert arg64 >= arg32 + 4 * n
